@@ -1,0 +1,245 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix (CPU only).
+
+Each test names the passage it follows.  The pins are chosen so that a plausible slip in
+the oracle -- a period of 2T instead of 2T+1, a dropped k = 0 term, a sign in the sine
+channels, a transposed image axis, a wrong boundary rule -- fails at least one of them.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import ndimage
+
+import oracle
+from oracle import fit, filters
+from paper_1811_02168_gb300.synth import voronoi_image
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden(name):
+    with open(os.path.join(GOLDEN, name)) as fh:
+        return json.load(fh)
+
+
+# ----------------------------------------------------------------------------- fitter
+
+def test_fig1_argmin_T_is_203():
+    """Fig. 1: for K = 4, R = 255, sigma = 50, E(4,T) is smallest at T = 203."""
+    g = _golden("fig1_err_vs_T.json")
+    b = fit.kernel_samples(g["sigma"], g["R"])
+    T_star, E_star, _, curve = fit.optimal_period(g["K"], b, g["R"])
+    assert T_star == g["argmin_T"]
+    for Tp in g["poor_T"]:
+        assert curve[Tp - 1] > 50.0 * E_star      # "visibly poor"
+    # unimodal around the optimum (Section II: E(K,T) is unimodal in T)
+    seg = curve[100:600]
+    k = int(np.argmin(seg))
+    assert np.all(np.diff(seg[:k]) <= 1e-12) and np.all(np.diff(seg[k:]) >= -1e-12)
+
+
+def test_ls_closed_form_at_T_equals_R():
+    """With T = R the K columns are samples of a length-(2R+1) DFT basis and are
+    orthogonal on Lambda, so least squares reduces to inner products:
+    c_0 = sum b / (2R+1), c_k = 2 sum_t b(t) cos(nu t k) / (2R+1).  This holds only for the
+    paper's division by 2T+1 in eq. (3) (a period of 2T breaks the orthogonality)."""
+    R, sigma, K = 255, 40.0, 9
+    b = fit.kernel_samples(sigma, R)
+    E, c = fit.kernel_error(K, R, b, R)
+    t = np.arange(-R, R + 1)
+    N = 2 * R + 1
+    expect = np.array([b.sum() / N] +
+                      [2.0 * np.sum(b * np.cos(2 * np.pi * t * k / N)) / N for k in range(1, K)])
+    np.testing.assert_allclose(c, expect, rtol=0, atol=1e-13)
+    # residual energy = ||b||^2 - sum of captured energy (Parseval on Lambda)
+    captured = N * expect[0] ** 2 + (N / 2.0) * np.sum(expect[1:] ** 2)
+    assert abs(E - (b @ b - captured)) < 1e-10
+
+
+def test_prop2_error_vanishes_at_T_R_K_R_plus_1():
+    """Prop. 2: the error vanishes for enough terms.  At T = R the R+1 cosines span all
+    even functions on Lambda, so E(R+1, R) = 0 already."""
+    R = 255
+    for sigma in (10.0, 80.0):
+        b = fit.kernel_samples(sigma, R)
+        E, _ = fit.kernel_error(R + 1, R, b, R)
+        assert E < 1e-20
+
+
+def test_K1_is_mean():
+    """K = 1: phi_hat is the constant c_0, so c_0 = mean(b), E = sum (b - mean)^2 for any T."""
+    R, sigma = 255, 30.0
+    b = fit.kernel_samples(sigma, R)
+    for T in (1, 7, 300):
+        E, c = fit.kernel_error(1, T, b, R)
+        assert abs(c[0] - b.mean()) < 1e-14
+        assert abs(E - np.sum((b - b.mean()) ** 2)) < 1e-11
+
+
+def test_prop2_monotone_in_K():
+    """Prop. 2: e(K+1) <= e(K)."""
+    R, sigma = 255, 30.0
+    b = fit.kernel_samples(sigma, R)
+    e = [fit.optimal_period(K, b, R)[1] for K in range(1, 9)]
+    assert all(e[i + 1] <= e[i] * (1 + 1e-9) + 1e-25 for i in range(len(e) - 1))
+    assert e[-1] < 1e-3 * e[0]
+
+
+def test_algorithm1_trends():
+    """Algorithm 1 + Fig. 2 trends: for fixed eps, K* falls and T* rises as sigma grows;
+    for fixed sigma, K* grows as eps shrinks.  The result satisfies e(K*) <= eps and
+    e(K*-1) > eps."""
+    R = 255
+    res = {}
+    for sigma in (10.0, 30.0, 80.0):
+        p = fit.make_plan(sigma, R, eps=0.01)
+        b = fit.kernel_samples(sigma, R)
+        assert p.E <= 0.01
+        if p.K > 1:
+            assert fit.optimal_period(p.K - 1, b, R)[1] > 0.01
+        res[sigma] = p
+    assert res[10.0].K > res[30.0].K > res[80.0].K
+    assert res[10.0].T < res[30.0].T < res[80.0].T
+    p3 = fit.make_plan(30.0, R, eps=1e-3)
+    assert p3.K > res[30.0].K
+
+
+def test_roundoff_floor_picks_smallest_T():
+    """Reading of the tie rule: at FP64 round-off the smallest T reaching the floor is taken."""
+    R = 255
+    b = fit.kernel_samples(80.0, R)
+    T_star, E_star, _, curve = fit.optimal_period(16, b, R)
+    floor = fit.ROUNDOFF_FLOOR_REL * float(b @ b)
+    fl = np.maximum(curve, floor)
+    assert fl[T_star - 1] == fl.min()
+    assert np.all(fl[:T_star - 1] > fl.min())
+
+
+# ----------------------------------------------------------------------------- filters
+
+def _img(H, W, seed=7, cells=12):
+    return voronoi_image(H, W, cells, ramp=30.0, noise_std=8.0, seed=seed).astype(np.float64)
+
+
+def test_spatial_radius():
+    """Window (6 theta + 1)^2 (Section I cost model): r = 3 theta for integer theta."""
+    assert [filters.spatial_radius(t) for t in (1, 2, 3, 5, 10)] == [3, 6, 9, 15, 30]
+    assert filters.spatial_radius(1.5) == 5 and filters.spatial_radius(0.4) == 2
+
+
+def test_brute_constant_image_unchanged():
+    """Eq. (1) is a normalised average: a constant image is a fixed point."""
+    f = np.full((9, 14), 117.0)
+    out = filters.brute_bf(f, 2.0, 30.0)
+    np.testing.assert_allclose(out, f, atol=1e-12)
+
+
+def _scipy_normalised_blur(f, theta):
+    """(omega*f)/(omega*1) with scipy's own Gaussian (sd theta, radius int(3 theta + 0.5),
+    zero padding); the normalisation of scipy's kernel cancels in the ratio."""
+    kw = dict(sigma=theta, truncate=3.0, mode="constant", cval=0.0)
+    return ndimage.gaussian_filter(f, **kw) / ndimage.gaussian_filter(np.ones_like(f), **kw)
+
+
+def test_brute_large_sigma_is_gaussian_blur():
+    """sigma -> infinity: phi == 1 and eq. (1) is the zero-padded normalised Gaussian blur
+    with the spatial kernel of eq. (2), here scipy.ndimage.gaussian_filter."""
+    f = _img(11, 16)
+    for theta in (1.0, 2.0):
+        out = filters.brute_bf(f, theta, 1e9)
+        np.testing.assert_allclose(out, _scipy_normalised_blur(f, theta), rtol=0, atol=1e-9)
+
+
+def test_brute_tiny_sigma_is_identity_on_integer_image():
+    """sigma -> 0: only neighbours with the same integer intensity keep weight, so f_BF = f."""
+    f = _img(10, 13)
+    out = filters.brute_bf(f, 2.0, 0.05)
+    np.testing.assert_allclose(out, f, atol=1e-10)
+
+
+def test_brute_step_edge_closed_form():
+    """Vertical step edge a | b.  In eq. (1) the y-sum of omega factors out of numerator and
+    denominator, leaving 1-D partial sums of g on each side of the edge:
+    f_BF = (f_i M_same + f_o phi(f_o - f_i) M_other) / (M_same + phi(f_o - f_i) M_other)."""
+    H, W, x0 = 7, 19, 8
+    a, bb = 40.0, 160.0
+    f = np.where(np.arange(W)[None, :] < x0, a, bb) * np.ones((H, 1))
+    theta, sigma = 2.0, 70.0
+    g = filters.spatial_taps(theta)
+    r = (len(g) - 1) // 2
+    phi = math.exp(-((bb - a) ** 2) / (2 * sigma * sigma))
+    out = filters.brute_bf(f, theta, sigma)
+    for x in range(W):
+        same = other = 0.0
+        for jx in range(-r, r + 1):
+            q = x - jx
+            if 0 <= q < W:
+                if (q < x0) == (x < x0):
+                    same += g[jx + r]
+                else:
+                    other += g[jx + r]
+        fi, fo = (a, bb) if x < x0 else (bb, a)
+        expect = (fi * same + fo * phi * other) / (same + phi * other)
+        np.testing.assert_allclose(out[:, x], expect, rtol=0, atol=1e-10)
+
+
+@pytest.mark.parametrize("shape,theta,K", [((13, 17), 2.0, 5), ((8, 21), 1.0, 3), ((19, 6), 1.5, 7)])
+def test_fourier_equals_brute_with_phi_hat(shape, theta, K):
+    """Section II (after eq. 3): with phi_hat as range kernel, eq. (1) equals the
+    convolution (channel) form.  Brute force with phi_hat is computed by a different route
+    (direct window sums), on non-square images so a transposed axis fails."""
+    f = _img(*shape)
+    p = fit.make_plan(30.0, 255, K=K)
+    fast = filters.fourier_bf(f, theta, p.c, p.T)
+    slow = filters.brute_bf(f, theta, range_fn=lambda t: fit.phi_hat(t, p.c, p.T))
+    np.testing.assert_allclose(fast, slow, rtol=0, atol=1e-9)
+    pts = [(0, 0), (shape[0] - 1, shape[1] - 1), (shape[0] // 2, 1), (2, shape[1] // 2)]
+    at = filters.fourier_bf_at(f, theta, p.c, p.T, pts)
+    np.testing.assert_allclose(at, [slow[y, x] for y, x in pts], rtol=0, atol=1e-9)
+
+
+def test_fourier_K1_is_normalised_blur():
+    """K = 1: phi_hat = c_0 is constant and eq. (1) reduces to (omega*f)/(omega*1)."""
+    f = _img(12, 15)
+    p = fit.make_plan(30.0, 255, K=1)
+    out = filters.fourier_bf(f, 2.0, p.c, p.T)
+    np.testing.assert_allclose(out, _scipy_normalised_blur(f, 2.0), rtol=0, atol=1e-9)
+
+
+def test_fourier_converges_to_brute_and_prop1_bound():
+    """Prop. 1 / Prop. 2: the filtering error is bounded through the kernel error and goes
+    to zero with it; at T = R, K = R + 1 the kernel is exact on Lambda and so is the filter."""
+    f = _img(12, 12, cells=6)
+    theta, sigma, R = 1.0, 30.0, 255
+    exact = filters.brute_bf(f, theta, sigma)
+    errs = []
+    for K in (3, 5, 8, 12):
+        p = fit.make_plan(sigma, R, K=K)
+        out = filters.fourier_bf(f, theta, p.c, p.T)
+        err = float(np.max(np.abs(out - exact)))
+        bound = filters.prop1_bound(R, p.delta_max, theta)
+        assert err <= bound
+        errs.append(err)
+    assert errs[-1] < errs[0]
+    p = fit.make_plan(sigma, R, K=R + 1, T=R)
+    out = filters.fourier_bf(f, theta, p.c, p.T)
+    np.testing.assert_allclose(out, exact, rtol=0, atol=1e-8)
+
+
+def test_psnr_band_at_eps_0_1():
+    """Section III: PSNR against brute force stays above 40 dB even at eps = 0.1."""
+    g = _golden("table1_psnr.json")
+    f = voronoi_image(48, 48, 10, ramp=40.0, noise_std=10.0, seed=11).astype(np.float64)
+    for sigma in (15.0, 30.0, 50.0):
+        p = fit.make_plan(sigma, 255, eps=0.1)
+        out = filters.fourier_bf(f, 2.0, p.c, p.T)
+        ref = filters.brute_bf(f, 2.0, sigma)
+        assert filters.psnr(out, ref) > g["min_psnr_db_at_eps_0.1"]
+
+
+def test_psnr_definition():
+    """PSNR = 10 log10(255^2/MSE) (Section III): MSE 1 gives 48.13 dB."""
+    a = np.zeros((4, 4))
+    assert abs(filters.psnr(a, a + 1.0) - 10 * math.log10(255.0 ** 2)) < 1e-12
