@@ -1,0 +1,375 @@
+#!/usr/bin/env python
+"""Benchmark: Mpix/s of Fourier bilateral filtering on one GB300 at a stated error against
+the FP64 oracle.
+
+Default workload (the sigma sweep): one 1024 x 1024 synthetic 8-bit image (Voronoi mosaic,
+200 cells, ramp 40, noise 10, seed 1000), theta = 5 (31 x 31 window), sigma in
+{10, 30, 80}, K chosen by Algorithm 1 at eps = 0.01, FP32 form.  One step filters the
+image once per sigma (3 launches, 3.15 Mpix).  Inputs are resident in HBM; L2 is flushed
+(256 MiB write) before every timed step, outside the timed region.
+
+Output: one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle instead
+(bounded sample per step) with the same metric and config.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Mpix/s on 1 GB300 at stated error vs FP64 oracle; served p50/p99 latency"
+TOL_FP32 = 5e-3
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["sigma_sweep", "small", "large"], default="sigma_sweep")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-rows", type=int, default=96, help="oracle sample: rows per sigma")
+    return ap.parse_args()
+
+
+def _jobs(name):
+    from paper_1811_02168_gb300 import synth
+    if name == "sigma_sweep":
+        return "sigma_sweep_1024x1024_theta5", synth.workload_sigma_sweep()
+    if name == "small":
+        return "small_256x256_theta3_sigma30_K4", [synth.workload_small()]
+    return "large_4096x4096_theta10_sigma10_K16", [synth.workload_large()]
+
+
+def _flops_per_px(K: int, r: int) -> float:
+    """Algorithmic work per output pixel: 4K-3 blurred images, 2 passes of 2r+1 taps,
+    2 flop per tap, plus ~16K for generation and recombination."""
+    return 4.0 * (4 * K - 3) * (2 * r + 1) + 16.0 * K
+
+
+def _fp32_peak_tflops(sm_count: int) -> tuple[float, str]:
+    mhz = 2070.0
+    src = "nominal max SM clock 2070 MHz"
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            mp = json.load(fh)
+        if mp.get("sm_max_mhz"):
+            mhz = float(mp["sm_max_mhz"])
+            src = "MEASURED_PEAKS.json sm_max_mhz"
+    except Exception:
+        pass
+    return sm_count * 128 * 2 * mhz * 1e6 / 1e12, f"{sm_count} SMs x 128 FP32 lanes x 2 flop x {mhz:.0f} MHz ({src})"
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.path = tempfile.mktemp(prefix="fbf_clocks_", suffix=".csv")
+        self.proc = None
+        self.gpu = gpu_index
+        self.t0 = self.t1 = None
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu=timestamp,{self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "50"], stdout=self.fh,
+                stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+
+    def mark(self, which):
+        setattr(self, which, time.time())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.1)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 10:
+                continue
+            rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        mx = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for i, nm in enumerate(names):
+                if r[6 + i].lower().startswith("active"):
+                    reasons.add(nm)
+        load = sorted(sm)[len(sm) // 2:] if sm else []
+        return {"sm_mhz": statistics.median(load) if load else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(rows), "window": "warm-up + timed region (50 ms sampling)"}
+
+
+def _traffic_for(kernel_file: str):
+    """Per-launch DRAM bytes from the committed ncu summary, if it was taken on the
+    current kernel source; else None."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+            t = json.load(fh)
+        src = open(os.path.join(ROOT, "paper_1811_02168_gb300", "csrc", kernel_file), "rb").read()
+        if t.get("kernel_sha256") == hashlib.sha256(src).hexdigest():
+            return t
+    except Exception:
+        pass
+    return None
+
+
+_ORACLE_PLANS = {}
+
+
+def _oracle_band(img, job, rows):
+    """FP64 oracle on the first `rows` rows (plus halo) of the image; returns the rows
+    whose window does not see the band's artificial lower edge, and the seconds taken."""
+    import numpy as np
+    from oracle import fit as ofit, filters as ofl
+    r = ofl.spatial_radius(job.theta)
+    band = img[: min(img.shape[0], rows + r)].astype(np.float64)
+    key = (job.sigma, job.K, job.eps)
+    if key not in _ORACLE_PLANS:
+        _ORACLE_PLANS[key] = ofit.make_plan(job.sigma, 255, K=job.K, eps=job.eps)
+    plan = _ORACLE_PLANS[key]
+    t0 = time.perf_counter()
+    out = ofl.fourier_bf(band, job.theta, plan.c, plan.T)
+    dt = time.perf_counter() - t0
+    keep = min(rows, img.shape[0])
+    if band.shape[0] < img.shape[0]:
+        keep = min(keep, band.shape[0] - r)
+    return out[:keep], dt
+
+
+def run_reference(a):
+    """Reference arm: the FP64 NumPy oracle on the host cores, as it stands."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import numpy as np
+    name, jobs = _jobs(a.workload)
+    imgs = {}
+    for j in jobs:
+        if j.seed not in imgs:
+            imgs[j.seed] = j.image()
+    rows = max(8, a.cpu_rows // 3)
+    per = []
+    for s in range(a.warmup + a.steps):
+        t = 0.0
+        px = 0
+        for j in jobs:
+            out, dt = _oracle_band(imgs[j.seed], j, rows)
+            t += dt
+            px += rows * j.W
+        if s >= a.warmup:
+            per.append((px, t))
+    px = sum(p for p, _ in per)
+    sec = sum(t for _, t in per)
+    val = px / sec / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "Mpix/s", "n_gpus": a.gpus,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * sec / len(per),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": _config(name, jobs, None, "oracle"),
+        "cpu_baseline": {"value": val, "unit": "Mpix/s", "cores": 1, "kind": "oracle",
+                         "sample": f"per step: first {rows} rows (+halo) of the image for each sigma"},
+        "e2e": {"value": val, "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _config(name, jobs, plans, form):
+    cfg = {"workload": name, "form": form,
+           "images": [{"H": j.H, "W": j.W, "theta": j.theta, "sigma": j.sigma,
+                       "K_req": j.K, "eps": j.eps} for j in jobs],
+           "l2": "flushed before each timed step (256 MiB write, untimed)"}
+    if plans:
+        for d, p in zip(cfg["images"], plans):
+            d["K"], d["T"], d["E"], d["r"] = p.K, p.T, p.E, p.radius
+    return cfg
+
+
+def run_ours(a):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1811_02168_gb300 import binding as B
+
+    name, jobs = _jobs(a.workload)
+    plans = [B.Plan(j.sigma, 255, j.theta, K=j.K or 0, eps=j.eps or 0.0) for j in jobs]
+    imgs_np = {}
+    for j in jobs:
+        if j.seed not in imgs_np:
+            imgs_np[j.seed] = j.image()
+    x = {s: torch.from_numpy(v).to(dev) for s, v in imgs_np.items()}
+    outs = [torch.empty((j.H, j.W), dtype=torch.float32, device=dev) for j in jobs]
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MiB
+    stream = torch.cuda.current_stream(dev)
+    sh = stream.cuda_stream
+    px_step = sum(j.H * j.W for j in jobs)
+    flops = [_flops_per_px(p.K, p.radius) * j.H * j.W for p, j in zip(plans, jobs)]
+
+    def step(evs=None):
+        for i, (p, j) in enumerate(zip(plans, jobs)):
+            if evs:
+                evs[i][0].record(stream)
+            B.fbf_filter(p.handle, x[j.seed].data_ptr(), outs[i].data_ptr(), j.H, j.W, j.W, sh)
+            if evs:
+                evs[i][1].record(stream)
+
+    clocks = ClockSampler(local)
+    if rank == 0:
+        clocks.start()
+    for _ in range(a.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    E = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    st_ev = [(E(), E()) for _ in range(a.steps)]
+    ln_ev = [[(E(), E()) for _ in jobs] for _ in range(a.steps)]
+    t_wall0 = time.perf_counter()
+    for s in range(a.steps):
+        flush.zero_()
+        st_ev[s][0].record(stream)
+        step(ln_ev[s])
+        st_ev[s][1].record(stream)
+    torch.cuda.synchronize(dev)
+    t_wall = time.perf_counter() - t_wall0
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    step_ms = [b.elapsed_time(e) for b, e in st_ev]
+    launch_ms = [statistics.mean(ln_ev[s][i][0].elapsed_time(ln_ev[s][i][1]) for s in range(a.steps))
+                 for i in range(len(jobs))]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * px_step * a.steps / (total_ms / 1e3) / 1e6
+
+    # ---- end to end through the public API with host buffers --------------------------
+    host_in = {s: torch.from_numpy(v).pin_memory() for s, v in imgs_np.items()}
+    host_out = [torch.empty((j.H, j.W), dtype=torch.float32).pin_memory() for j in jobs]
+    e2e_steps = max(3, min(a.steps, 50))
+    for _ in range(2):
+        for i, (p, j) in enumerate(zip(plans, jobs)):
+            B.bilateral_filter(p, host_in[j.seed], out=host_out[i])
+    e2e_t = []
+    for _ in range(e2e_steps):
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for i, (p, j) in enumerate(zip(plans, jobs)):
+            B.bilateral_filter(p, host_in[j.seed], out=host_out[i])
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_sec = sum(e2e_t)
+    if world > 1:
+        t = torch.tensor([e2e_sec], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_sec = float(t.item())
+    e2e_val = world * px_step * e2e_steps / e2e_sec / 1e6
+    h2d = sum(4 * j.H * j.W for j in jobs)
+    d2h = sum(4 * j.H * j.W for j in jobs)
+    clk = clocks.stop() if rank == 0 else None
+
+    # ---- roofline of the fused kernel ---------------------------------------------------
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak, peak_src = _fp32_peak_tflops(sm_count)
+    achieved = sum(flops) / (sum(launch_ms) / 1e3) / 1e12
+    tr = _traffic_for("fbf_fp32.cu")
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": None, "kernel": "fbf_fp32_kernel",
+            "peak_source": peak_src + " (derived FP32 FFMA peak)",
+            "flops_per_px": [_flops_per_px(p.K, p.radius) for p in plans],
+            "launch_ms": launch_ms}
+    if tr and name in tr.get("workloads", {}):
+        roof["traffic"] = tr["workloads"][name]
+
+    result = {
+        "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": _config(name, jobs, plans, "fp32"), "roofline": roof,
+        "e2e": {"value": e2e_val, "unit": "Mpix/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "steps": e2e_steps},
+        "gpu_launches": a.steps * len(jobs), "clocks": clk,
+        "timed_wall_s": t_wall,
+    }
+
+    # ---- CPU baseline: the oracle as it stands, on a bounded sample (rank 0, N = 1) -----
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        cpu_px = 0
+        cpu_s = 0.0
+        errs = []
+        for i, j in enumerate(jobs):
+            ref, dt = _oracle_band(imgs_np[j.seed], j, a.cpu_rows)
+            cpu_s += dt
+            cpu_px += ref.shape[0] * j.W
+            got = outs[i][: ref.shape[0]].cpu().numpy()
+            errs.append(float(np.abs(got - ref).max()))
+        result["cpu_baseline"] = {
+            "value": cpu_px / cpu_s / 1e6, "unit": "Mpix/s", "cores": 1, "kind": "oracle",
+            "sample": f"FP64 NumPy Fourier oracle on the first {a.cpu_rows} rows (+halo) of the "
+                      f"image for each sigma; single-threaded NumPy"}
+        result["error_vs_oracle"] = {"max_abs": max(errs), "per_image": errs, "tolerance": TOL_FP32,
+                                     "sample": f"first {a.cpu_rows} rows of each output"}
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    a = _args()
+    if a.impl == "reference":
+        return run_reference(a)
+    return run_ours(a)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

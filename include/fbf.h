@@ -1,0 +1,131 @@
+/*
+ * fbf.h -- C ABI of the GB300 (sm_103a) Fourier bilateral filter.
+ *
+ * Method: Optimized Fourier Bilateral Filtering (Ghosh, Nair, Chaudhury, IEEE Signal
+ * Processing Letters 25(10), 2018).  The bilateral filter of eq. (1), with the Gaussian
+ * kernels of eq. (2), is computed with the range kernel replaced by the K-term cosine
+ * series of eq. (3), phi_hat(t) = sum_{k<K} c_k cos(2 pi k t / (2T+1)).  The period T and
+ * the coefficients c are fitted on the host in FP64 by least squares on the integer
+ * differences t in {-R..R} (eqs. (4)-(6), Algorithm 1).  On the device, numerator and
+ * denominator of eq. (1) become Gaussian convolutions of the images cos(k nu f),
+ * sin(k nu f), f cos(k nu f), f sin(k nu f) (Section II, the remark after eq. (3)); the
+ * kernels generate those images per tile, blur them and recombine them in one pass, so
+ * only f is read from and only f_BF is written to device memory.
+ *
+ * Conventions for every entry point:
+ *   - Return value: FBF_OK (0) or one of the FBF_E* codes below.  No C++ exception
+ *     crosses this boundary.  fbf_last_error() gives a message for the calling thread.
+ *   - Images are single-channel float32, row-major, values in [0, R].  Integer values
+ *     (8-bit images converted to float) are the case the paper treats (Lambda holds only
+ *     integers, Section II); other values are filtered with the same formula.
+ *   - Device pointers are owned by the caller, who keeps them alive until the work that
+ *     uses them has completed (stream order, or fbf_poll reporting FBF_DONE).
+ *   - Neighbours outside the image are absent from both sums of eq. (1) (zero padding of
+ *     every convolved image, including the constant one).
+ *   - A pixel whose denominator comes out <= 0 keeps its input value.
+ */
+#ifndef FBF_H
+#define FBF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ------------------------------------------------------------- */
+#define FBF_OK         0
+#define FBF_EINVAL     1   /* bad argument (see each function)                       */
+#define FBF_ENOMEM     2   /* host or device allocation failed                       */
+#define FBF_ECUDA      3   /* a CUDA runtime call failed (message in fbf_last_error)  */
+#define FBF_ETIMEDOUT  4   /* a bounded wait gave up                                 */
+#define FBF_EBUSY      5   /* admission refused: no free slot or over the budget     */
+#define FBF_PENDING    6   /* fbf_poll status: submitted work not finished yet        */
+#define FBF_DONE       7   /* fbf_poll status: finished                              */
+#define FBF_EUNSUPPORTED 8 /* valid request outside what the kernels are built for   */
+
+/* ---- precision forms (fbf_plan's `precision`) --------------------------------- */
+#define FBF_FP32       0   /* FP32 channel stack and FP32 FIR on the CUDA cores       */
+
+/* ---- flags (fbf_plan's `flags`) ----------------------------------------------- */
+#define FBF_FLAG_FIXED_PERIOD 1  /* T = R (fixed period, the FBF model the paper
+                                    compares against, Section III); least squares only */
+
+/* Limits of the device kernels. */
+#define FBF_MAX_K       64  /* cosine terms                                       */
+#define FBF_MAX_RADIUS  48  /* spatial radius r = ceil(3 theta)                   */
+#define FBF_MAX_PERIOD  65535 /* 2T+1                                             */
+
+typedef struct fbf_plan_s* fbf_plan_t;
+
+/*
+ * fbf_plan -- fit (K, T, c) for one (sigma, R, theta) and precompute the device constants.
+ *
+ * Section II: b(t) = exp(-t^2/(2 sigma^2)) on t in {-R..R} (eq. 2);
+ * A(t,k) = cos(nu t k), nu = 2 pi/(2T+1); E(K,T) = min_c ||A c - b||^2 (eq. 5).
+ *   K >= 1            : fixed order; T = argmin over T of E(K,T) (eq. 6, the Fig. 1 setting).
+ *   K == 0, eps > 0   : Algorithm 1 -- the smallest K with min_T E(K,T) <= eps.
+ * T is searched over 1..T_max, T_max = 4R, doubled while the optimum lies above T_max/2.
+ * Among T whose error is at FP64 round-off (below 1e-20 ||b||^2) the smallest is taken.
+ * Rank-deficient systems (K > T+1) are solved with dependent columns dropped; phi_hat on
+ * {-R..R} is the same for every least-squares solution.
+ *
+ * sigma > 0, R >= 1, theta > 0 (spatial std; window radius r = ceil(3 theta), the
+ * (6 theta + 1)^2 window of Section I), precision one of FBF_FP32..., flags a bitwise OR
+ * of FBF_FLAG_*.  Runs on the host only; needs no GPU.  *out receives a handle owned by
+ * the caller and released with fbf_plan_destroy.
+ * Errors: FBF_EINVAL for bad arguments or a NULL out; FBF_EUNSUPPORTED when the fitted
+ * K exceeds FBF_MAX_K, r exceeds FBF_MAX_RADIUS or 2T+1 exceeds FBF_MAX_PERIOD;
+ * FBF_ENOMEM.
+ */
+int fbf_plan(fbf_plan_t* out, double sigma, int R, double theta, int K, double eps,
+             int precision, int flags);
+
+/*
+ * fbf_plan_from_samples -- as fbf_plan, for an arbitrary range kernel given by its
+ * samples b[0..2R] = phi(-R..R) (host pointer, read during the call only).  The paper
+ * notes the least-squares fit applies to non-Gaussian kernels (Sections I and IV).  Only
+ * the even part of b can be represented by the cosine series; E includes the odd part's
+ * energy.  phi(0) = b[R] must be > 0.
+ */
+int fbf_plan_from_samples(fbf_plan_t* out, const double* b, int R, double theta, int K,
+                          double eps, int precision, int flags);
+
+/*
+ * fbf_plan_info -- read back the fitted parameters.  Any output pointer may be NULL.
+ * c receives K doubles (c_0..c_{K-1} of eq. 3); E = E(K,T) of eq. (5);
+ * delta_max = max over t in {-R..R} of |phi_hat(t) - phi(t)|.
+ */
+int fbf_plan_info(fbf_plan_t plan, int* K, int* T, double* c, double* E, double* delta_max);
+
+/* fbf_plan_radius -- spatial radius r = ceil(3 theta) used by the kernels. */
+int fbf_plan_radius(fbf_plan_t plan, int* r);
+
+/* fbf_plan_destroy -- release a plan (NULL is accepted).  The caller makes sure no
+ * launched work still uses it (plans hold no device memory; kernels receive their
+ * constants by value at launch, so a plan may be destroyed right after a launch). */
+int fbf_plan_destroy(fbf_plan_t plan);
+
+/*
+ * fbf_filter -- f_BF of eq. (1) with phi_hat, for one H x W image, asynchronously on
+ * `cuda_stream` (a cudaStream_t; NULL means the legacy default stream).
+ *
+ * d_in, d_out: device pointers to H x W float32 images with a row stride of pitch_elems
+ * elements (pitch_elems >= W); in and out must not overlap.  H, W >= 1; H*W may be
+ * anything the device memory holds.  Launch errors are reported as FBF_ECUDA; errors of
+ * the asynchronous work surface at the caller's next synchronisation.
+ */
+int fbf_filter(fbf_plan_t plan, const float* d_in, float* d_out, int H, int W,
+               size_t pitch_elems, void* cuda_stream);
+
+/* fbf_last_error -- message for the last failing call on this thread ("" if none). */
+const char* fbf_last_error(void);
+
+/* fbf_version -- library version string. */
+const char* fbf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FBF_H */

@@ -51,11 +51,17 @@ def kernel_samples(sigma: float, R: int, kernel=None):
 
 
 def design_matrix(K: int, T: int, R: int):
-    """A(i,j) = cos(nu (i-R-1)(j-1)), nu = 2 pi/(2T+1), size (2R+1) x K (Section II)."""
-    nu = 2.0 * math.pi / (2 * T + 1)
-    t = np.arange(-R, R + 1, dtype=np.float64)[:, None]
-    k = np.arange(K, dtype=np.float64)[None, :]
-    return np.cos(nu * t * k)
+    """A(i,j) = cos(nu (i-R-1)(j-1)), nu = 2 pi/(2T+1), size (2R+1) x K (Section II).
+
+    t = i-R-1 and k = j-1 are integers, so the angle nu t k is reduced exactly, as the
+    integer (t k) mod (2T+1) times nu.  Columns that coincide in exact arithmetic
+    (k and 2T+1-k when K > T+1) then coincide in floating point too; evaluating cos at
+    the unreduced angle leaves ~1e-13 differences that least squares would fit.
+    """
+    P = 2 * T + 1
+    t = np.arange(-R, R + 1, dtype=np.int64)[:, None]
+    k = np.arange(K, dtype=np.int64)[None, :]
+    return np.cos((2.0 * math.pi / P) * np.mod(t * k, P).astype(np.float64))
 
 
 def kernel_error(K: int, T: int, b, R: int):
@@ -121,10 +127,16 @@ def algorithm1(b, R: int, eps: float, T_max: int | None = None, K_limit: int | N
 def phi_hat(t, c, T: int):
     """phi_hat(t) = sum_k c_k cos(2 pi k t/(2T+1)), eq. (3)."""
     t = np.asarray(t, dtype=np.float64)
-    nu = 2.0 * math.pi / (2 * T + 1)
+    P = 2 * T + 1
+    nu = 2.0 * math.pi / P
+    integral = bool(np.all(t == np.round(t))) and t.size > 0 and np.max(np.abs(t)) < 2 ** 40
     out = np.zeros_like(t)
     for k, ck in enumerate(np.asarray(c, dtype=np.float64)):
-        out = out + ck * np.cos(nu * k * t)
+        if integral:   # exact reduction of the angle, as in design_matrix
+            ang = nu * np.mod(np.round(t).astype(np.int64) * k, P).astype(np.float64)
+        else:
+            ang = nu * k * t
+        out = out + ck * np.cos(ang)
     return out
 
 

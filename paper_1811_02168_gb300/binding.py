@@ -1,0 +1,203 @@
+"""Thin Python binding of ``libfbf.so`` (ctypes).  Argument marshalling only: every step
+of the filter runs in the library's kernels; PyTorch provides device memory and streams.
+
+The functions mirror the C ABI in ``include/fbf.h`` name for name (``fbf_plan``,
+``fbf_filter``, ...), raising :class:`FbfError` on a non-zero return code.  ``Plan`` and
+``bilateral_filter`` are small conveniences on top.
+There is no fallback: if the library is missing or cannot be loaded, loading raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfbf.so")
+
+FBF_OK, FBF_EINVAL, FBF_ENOMEM, FBF_ECUDA, FBF_ETIMEDOUT, FBF_EBUSY = 0, 1, 2, 3, 4, 5
+FBF_PENDING, FBF_DONE, FBF_EUNSUPPORTED = 6, 7, 8
+FBF_FP32 = 0
+FBF_FLAG_FIXED_PERIOD = 1
+FBF_MAX_K = 64
+FBF_MAX_RADIUS = 48
+
+_CODES = {0: "FBF_OK", 1: "FBF_EINVAL", 2: "FBF_ENOMEM", 3: "FBF_ECUDA", 4: "FBF_ETIMEDOUT",
+          5: "FBF_EBUSY", 6: "FBF_PENDING", 7: "FBF_DONE", 8: "FBF_EUNSUPPORTED"}
+
+
+class FbfError(RuntimeError):
+    def __init__(self, code: int, func: str, msg: str):
+        super().__init__(f"{func} -> {_CODES.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+_lock = threading.Lock()
+
+_c_double_p = ctypes.POINTER(ctypes.c_double)
+_c_int_p = ctypes.POINTER(ctypes.c_int)
+_c_void_pp = ctypes.POINTER(ctypes.c_void_p)
+
+# name -> (restype, argtypes); mirrors include/fbf.h
+SIGNATURES = {
+    "fbf_plan": (ctypes.c_int, [_c_void_pp, ctypes.c_double, ctypes.c_int, ctypes.c_double,
+                                ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int]),
+    "fbf_plan_from_samples": (ctypes.c_int, [_c_void_pp, _c_double_p, ctypes.c_int, ctypes.c_double,
+                                             ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int]),
+    "fbf_plan_info": (ctypes.c_int, [ctypes.c_void_p, _c_int_p, _c_int_p, _c_double_p, _c_double_p,
+                                     _c_double_p]),
+    "fbf_plan_radius": (ctypes.c_int, [ctypes.c_void_p, _c_int_p]),
+    "fbf_plan_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "fbf_filter": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                  ctypes.c_int, ctypes.c_size_t, ctypes.c_void_p]),
+    "fbf_last_error": (ctypes.c_char_p, []),
+    "fbf_version": (ctypes.c_char_p, []),
+    "fbf_debug_error_curve": (ctypes.c_int, [_c_double_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                             _c_double_p]),
+}
+
+
+def lib() -> ctypes.CDLL:
+    """Load libfbf.so (once).  Raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError(f"{LIB_PATH} is missing: build it with "
+                                  "`python -c 'import __graft_entry__ as g; g.build()'`")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(rc: int, func: str):
+    if rc != FBF_OK:
+        raise FbfError(rc, func, lib().fbf_last_error().decode())
+
+
+# ----------------------------------------------------------------------------- ABI mirrors
+
+def fbf_plan(sigma: float, R: int, theta: float, K: int = 0, eps: float = 0.0,
+             precision: int = FBF_FP32, flags: int = 0) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().fbf_plan(ctypes.byref(h), sigma, R, theta, K, eps, precision, flags), "fbf_plan")
+    return h.value
+
+
+def fbf_plan_from_samples(b, R: int, theta: float, K: int = 0, eps: float = 0.0,
+                          precision: int = FBF_FP32, flags: int = 0) -> int:
+    arr = (ctypes.c_double * (2 * R + 1))(*[float(x) for x in b])
+    h = ctypes.c_void_p()
+    _check(lib().fbf_plan_from_samples(ctypes.byref(h), arr, R, theta, K, eps, precision, flags),
+           "fbf_plan_from_samples")
+    return h.value
+
+
+def fbf_plan_info(plan: int):
+    K, T = ctypes.c_int(), ctypes.c_int()
+    E, dm = ctypes.c_double(), ctypes.c_double()
+    _check(lib().fbf_plan_info(plan, ctypes.byref(K), ctypes.byref(T), None, ctypes.byref(E),
+                               ctypes.byref(dm)), "fbf_plan_info")
+    c = (ctypes.c_double * max(1, K.value))()
+    _check(lib().fbf_plan_info(plan, None, None, c, None, None), "fbf_plan_info")
+    return K.value, T.value, [c[i] for i in range(K.value)], E.value, dm.value
+
+
+def fbf_plan_radius(plan: int) -> int:
+    r = ctypes.c_int()
+    _check(lib().fbf_plan_radius(plan, ctypes.byref(r)), "fbf_plan_radius")
+    return r.value
+
+
+def fbf_plan_destroy(plan: int) -> None:
+    _check(lib().fbf_plan_destroy(plan), "fbf_plan_destroy")
+
+
+def fbf_filter(plan: int, d_in: int, d_out: int, H: int, W: int, pitch_elems: int,
+               stream: int = 0) -> None:
+    _check(lib().fbf_filter(plan, d_in, d_out, H, W, pitch_elems, stream), "fbf_filter")
+
+
+def fbf_last_error() -> str:
+    return lib().fbf_last_error().decode()
+
+
+def fbf_version() -> str:
+    return lib().fbf_version().decode()
+
+
+def fbf_debug_error_curve(b, R: int, T: int, Kc: int):
+    arr = (ctypes.c_double * (2 * R + 1))(*[float(x) for x in b])
+    out = (ctypes.c_double * Kc)()
+    _check(lib().fbf_debug_error_curve(arr, R, T, Kc, out), "fbf_debug_error_curve")
+    return [out[i] for i in range(Kc)]
+
+
+# ----------------------------------------------------------------------------- conveniences
+
+class Plan:
+    """Owns an ``fbf_plan_t``.  Fitted parameters are read back once."""
+
+    def __init__(self, sigma: float | None = None, R: int = 255, theta: float = 3.0, K: int = 0,
+                 eps: float = 0.0, precision: int = FBF_FP32, flags: int = 0, samples=None):
+        if samples is not None:
+            self.handle = fbf_plan_from_samples(samples, R, theta, K, eps, precision, flags)
+        else:
+            self.handle = fbf_plan(sigma, R, theta, K, eps, precision, flags)
+        self.sigma, self.R, self.theta, self.precision, self.flags = sigma, R, theta, precision, flags
+        self.K, self.T, self.c, self.E, self.delta_max = fbf_plan_info(self.handle)
+        self.radius = fbf_plan_radius(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            fbf_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __repr__(self):
+        return (f"Plan(sigma={self.sigma}, R={self.R}, theta={self.theta}, K={self.K}, T={self.T}, "
+                f"E={self.E:.3g}, precision={self.precision})")
+
+
+def bilateral_filter(plan: Plan, image, out=None, stream=None):
+    """f_BF of one 2-D float32 image.
+
+    ``image`` is a torch tensor.  On the GPU it is filtered in place of memory on the
+    current (or given) stream and a device tensor is returned.  On the host it is copied
+    to the device (pinned staging), filtered, and copied back: the end-to-end path.
+    """
+    import torch
+    if image.dim() != 2 or image.dtype != torch.float32:
+        raise ValueError("image must be a 2-D float32 tensor")
+    host = not image.is_cuda
+    if host:
+        src = image if image.is_pinned() else image.pin_memory()
+        dev_in = src.to("cuda", non_blocking=True)
+    else:
+        dev_in = image
+    if dev_in.stride(1) != 1:
+        dev_in = dev_in.contiguous()
+    H, W = dev_in.shape
+    dev_out = out if (out is not None and out.is_cuda) else torch.empty((H, W), device=dev_in.device,
+                                                                        dtype=torch.float32)
+    if dev_out.stride(0) != dev_in.stride(0) or dev_out.stride(1) != 1:
+        raise ValueError("out must have the input's row stride")
+    st = stream if stream is not None else torch.cuda.current_stream(dev_in.device)
+    fbf_filter(plan.handle, dev_in.data_ptr(), dev_out.data_ptr(), H, W, dev_in.stride(0),
+               st.cuda_stream)
+    if host:
+        res = out if out is not None else torch.empty((H, W), dtype=torch.float32, pin_memory=True)
+        res.copy_(dev_out, non_blocking=True)
+        st.synchronize()
+        return res
+    return dev_out

@@ -1,0 +1,172 @@
+// C ABI: plans, parameter read-back, errors (host only; the launches live in the .cu files).
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "fbf_internal.h"
+
+namespace fbf {
+
+static thread_local std::string g_last_error;
+
+int set_error(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+void clear_error() { g_last_error.clear(); }
+
+}  // namespace fbf
+
+using fbf::Plan;
+
+struct fbf_plan_s {
+  Plan p;
+};
+
+namespace {
+
+int radius_of(double theta) { return (int)std::ceil(3.0 * theta - 1e-12); }
+
+bool precision_known(int precision) {
+  return precision == FBF_FP32;
+}
+
+int build_plan(fbf_plan_t* out, const double* b, int R, double theta, int K, double eps,
+               int precision, int flags, double sigma) {
+  if (!out) return fbf::set_error(FBF_EINVAL, "fbf_plan: out is NULL");
+  *out = nullptr;
+  if (R < 1) return fbf::set_error(FBF_EINVAL, "fbf_plan: R must be >= 1");
+  if (!(theta > 0) || !std::isfinite(theta)) return fbf::set_error(FBF_EINVAL, "fbf_plan: theta must be > 0");
+  if (K < 0) return fbf::set_error(FBF_EINVAL, "fbf_plan: K must be >= 0");
+  if (K == 0 && !(eps > 0)) return fbf::set_error(FBF_EINVAL, "fbf_plan: K == 0 needs eps > 0");
+  if (!precision_known(precision)) return fbf::set_error(FBF_EINVAL, "fbf_plan: unknown precision form");
+  if (flags & ~FBF_FLAG_FIXED_PERIOD) return fbf::set_error(FBF_EINVAL, "fbf_plan: unknown flag");
+  if (!(b[R] > 0)) return fbf::set_error(FBF_EINVAL, "fbf_plan: phi(0) must be > 0");
+  const int r = radius_of(theta);
+  if (r > FBF_MAX_RADIUS)
+    return fbf::set_error(FBF_EUNSUPPORTED, "fbf_plan: radius ceil(3 theta) exceeds FBF_MAX_RADIUS");
+  if (K > FBF_MAX_K) return fbf::set_error(FBF_EUNSUPPORTED, "fbf_plan: K exceeds FBF_MAX_K");
+
+  fbf_plan_s* h = new (std::nothrow) fbf_plan_s();
+  if (!h) return fbf::set_error(FBF_ENOMEM, "fbf_plan: out of host memory");
+  Plan& p = h->p;
+  p.sigma = sigma;
+  p.theta = theta;
+  p.R = R;
+  p.r = r;
+  p.precision = precision;
+  p.flags = flags;
+  std::string msg;
+  int T_fixed = (flags & FBF_FLAG_FIXED_PERIOD) ? R : 0;
+  int rc = fbf::fit_range_kernel(b, R, K, eps, T_fixed, &p.fit, &msg);
+  if (rc != FBF_OK) { delete h; return fbf::set_error(rc, "fbf_plan: " + msg); }
+  if (p.fit.K > FBF_MAX_K) { delete h; return fbf::set_error(FBF_EUNSUPPORTED, "fbf_plan: fitted K exceeds FBF_MAX_K"); }
+  if (2L * p.fit.T + 1 > FBF_MAX_PERIOD) { delete h; return fbf::set_error(FBF_EUNSUPPORTED, "fbf_plan: period exceeds FBF_MAX_PERIOD"); }
+
+  // device constants
+  fbf::DeviceParams& d = p.dp;
+  std::memset(&d, 0, sizeof(d));
+  d.K = p.fit.K;
+  d.P = 2 * p.fit.T + 1;
+  d.r = r;
+  d.nu = (float)(2.0 * M_PI / (double)d.P);
+  d.invP = (float)(1.0 / (double)d.P);
+  d.center = (float)(0.5 * (double)R);
+  for (int k = 0; k < d.K; ++k) d.c[k] = (float)p.fit.c[k];
+  double gs = 0;
+  for (int i = -r; i <= r; ++i) gs += std::exp(-(double)i * i / (2.0 * theta * theta));
+  for (int i = -r; i <= r; ++i) d.g[i + r] = (float)(std::exp(-(double)i * i / (2.0 * theta * theta)) / gs);
+  *out = h;
+  fbf::clear_error();
+  return FBF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fbf_plan(fbf_plan_t* out, double sigma, int R, double theta, int K, double eps,
+             int precision, int flags) {
+  if (!(sigma > 0) || !std::isfinite(sigma)) {
+    if (out) *out = nullptr;
+    return fbf::set_error(FBF_EINVAL, "fbf_plan: sigma must be > 0");
+  }
+  if (R < 1 || R > (1 << 20)) {
+    if (out) *out = nullptr;
+    return fbf::set_error(FBF_EINVAL, "fbf_plan: R out of range");
+  }
+  std::string b_err;
+  double* b = new (std::nothrow) double[2 * R + 1];
+  if (!b) return fbf::set_error(FBF_ENOMEM, "fbf_plan: out of host memory");
+  for (int t = -R; t <= R; ++t) b[t + R] = std::exp(-(double)t * t / (2.0 * sigma * sigma));
+  int rc = build_plan(out, b, R, theta, K, eps, precision, flags, sigma);
+  delete[] b;
+  return rc;
+}
+
+int fbf_plan_from_samples(fbf_plan_t* out, const double* b, int R, double theta, int K,
+                          double eps, int precision, int flags) {
+  if (!b) {
+    if (out) *out = nullptr;
+    return fbf::set_error(FBF_EINVAL, "fbf_plan_from_samples: b is NULL");
+  }
+  if (R < 1 || R > (1 << 20)) {
+    if (out) *out = nullptr;
+    return fbf::set_error(FBF_EINVAL, "fbf_plan_from_samples: R out of range");
+  }
+  return build_plan(out, b, R, theta, K, eps, precision, flags, NAN);
+}
+
+int fbf_plan_info(fbf_plan_t plan, int* K, int* T, double* c, double* E, double* delta_max) {
+  if (!plan) return fbf::set_error(FBF_EINVAL, "fbf_plan_info: plan is NULL");
+  const fbf::FitResult& f = plan->p.fit;
+  if (K) *K = f.K;
+  if (T) *T = f.T;
+  if (c) for (int k = 0; k < f.K; ++k) c[k] = f.c[k];
+  if (E) *E = f.E;
+  if (delta_max) *delta_max = f.delta_max;
+  return FBF_OK;
+}
+
+int fbf_plan_radius(fbf_plan_t plan, int* r) {
+  if (!plan || !r) return fbf::set_error(FBF_EINVAL, "fbf_plan_radius: NULL argument");
+  *r = plan->p.r;
+  return FBF_OK;
+}
+
+int fbf_plan_destroy(fbf_plan_t plan) {
+  delete plan;
+  return FBF_OK;
+}
+
+int fbf_filter(fbf_plan_t plan, const float* d_in, float* d_out, int H, int W,
+               size_t pitch_elems, void* cuda_stream) {
+  if (!plan) return fbf::set_error(FBF_EINVAL, "fbf_filter: plan is NULL");
+  if (!d_in || !d_out) return fbf::set_error(FBF_EINVAL, "fbf_filter: NULL image pointer");
+  if (H < 1 || W < 1) return fbf::set_error(FBF_EINVAL, "fbf_filter: H and W must be >= 1");
+  if (pitch_elems < (size_t)W) return fbf::set_error(FBF_EINVAL, "fbf_filter: pitch < W");
+  const size_t span = ((size_t)(H - 1) * pitch_elems + (size_t)W) * sizeof(float);
+  const char* a = (const char*)d_in;
+  const char* o = (const char*)d_out;
+  if (a < o + span && o < a + span) return fbf::set_error(FBF_EINVAL, "fbf_filter: in and out overlap");
+  switch (plan->p.precision) {
+    case FBF_FP32:
+      return fbf::launch_fp32(plan->p.dp, d_in, d_out, H, W, pitch_elems, cuda_stream);
+    default:
+      return fbf::set_error(FBF_EINVAL, "fbf_filter: unknown precision form");
+  }
+}
+
+const char* fbf_last_error(void) { return fbf::g_last_error.c_str(); }
+
+const char* fbf_version(void) { return "fbf-gb300 0.1"; }
+
+// Test hook: E(K,T) for K = 1..Kc at one T from the C++ fitter (host only).
+int fbf_debug_error_curve(const double* b, int R, int T, int Kc, double* E_out) {
+  if (!b || !E_out || R < 1 || T < 1 || Kc < 1) return fbf::set_error(FBF_EINVAL, "bad argument");
+  fbf::kernel_error_curve(b, R, T, Kc, E_out);
+  return FBF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,63 @@
+// Internal declarations shared by the library's translation units (not part of the ABI).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "fbf.h"
+
+namespace fbf {
+
+// ---- host fitter (fbf_fit.cpp) --------------------------------------------------------
+struct FitResult {
+  int K = 0;                 // number of cosine terms
+  int T = 0;                 // period parameter: phi_hat has period 2T+1 (eq. 3)
+  std::vector<double> c;     // c_0..c_{K-1}
+  double E = 0.0;            // E(K,T) of eq. (5), including the odd part of b
+  double delta_max = 0.0;    // max over {-R..R} of |phi_hat - phi|
+};
+
+// b has 2R+1 samples phi(-R..R).  K >= 1: fixed order (T optimised unless T_fixed > 0).
+// K == 0: Algorithm 1 with tolerance eps.  Returns FBF_OK or an error code; msg is set on
+// error.
+int fit_range_kernel(const double* b, int R, int K, double eps, int T_fixed,
+                     FitResult* out, std::string* msg);
+
+// E(K,T) for K = 1..Kc at one T (folded Householder QR); used by tests via the C ABI.
+void kernel_error_curve(const double* b, int R, int T, int Kc, double* E_out);
+
+// ---- device parameters ----------------------------------------------------------------
+// Everything a filter kernel needs, passed by value at launch (constant bank), so plans
+// own no device memory.
+struct DeviceParams {
+  int K;                        // cosine terms
+  int P;                        // period 2T+1
+  int r;                        // spatial radius
+  int pad_;
+  float nu;                     // 2 pi / P
+  float invP;                   // 1 / P
+  float center;                 // m: f-channels carry (f - m); m is added back at the end
+  float pad2_;
+  float c[FBF_MAX_K];           // c_k (eq. 3)
+  float g[2 * FBF_MAX_RADIUS + 1];  // g[d] = exp(-(d-r)^2/(2 theta^2)) / sum, d = 0..2r
+};
+
+struct Plan {
+  double sigma = 0, theta = 0;
+  int R = 0, r = 0, precision = 0, flags = 0;
+  FitResult fit;
+  DeviceParams dp{};
+};
+
+// ---- errors ---------------------------------------------------------------------------
+int set_error(int code, const std::string& msg);
+void clear_error();
+
+// ---- kernels --------------------------------------------------------------------------
+// FP32 fused kernel launcher (fbf_fp32.cu).
+int launch_fp32(const DeviceParams& dp, const float* in, float* out, int H, int W,
+                size_t pitch, void* stream);
+
+}  // namespace fbf

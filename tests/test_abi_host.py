@@ -1,0 +1,167 @@
+"""C-ABI library on the host (no GPU): it loads, exports every symbol include/*.h
+declares, its FP64 fitter matches the oracle's, and bad arguments are rejected with the
+documented codes before any device work."""
+import ctypes
+import glob
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import fit as ofit
+from paper_1811_02168_gb300 import binding as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1811_02168_gb300 import build
+    build.build()
+    B.lib()
+
+
+def _declared_symbols():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(fbf_\w+)\s*\(", src, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_exports_every_declared_symbol():
+    names = _declared_symbols()
+    assert "fbf_plan" in names and "fbf_filter" in names
+    L = ctypes.CDLL(B.LIB_PATH)
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+    assert set(names) <= set(B.SIGNATURES), "binding lacks a mirror for a declared symbol"
+
+
+def _phi_hat(c, T, R):
+    t = np.arange(-R, R + 1)
+    return ofit.phi_hat(t, c, T)
+
+
+@pytest.mark.parametrize("sigma,K", [(50.0, 4), (30.0, 4), (10.0, 16), (80.0, 8), (15.0, 5)])
+def test_fitter_fixed_K_matches_oracle(sigma, K):
+    """eq. (5)/(6) with K fixed: same T, same E, same phi_hat on Lambda."""
+    R, theta = 255, 3.0
+    p = B.Plan(sigma, R, theta, K=K)
+    o = ofit.make_plan(sigma, R, K=K)
+    assert p.K == o.K == K
+    assert p.T == o.T
+    assert abs(p.E - o.E) <= 1e-9 * max(1.0, o.E) + 1e-14
+    np.testing.assert_allclose(_phi_hat(p.c, p.T, R), _phi_hat(o.c, o.T, R), rtol=0, atol=1e-10)
+    assert abs(p.delta_max - o.delta_max) < 1e-10
+
+
+def test_fitter_fig1_T203():
+    """Fig. 1: K = 4, sigma = 50, R = 255 gives T = 203."""
+    assert B.Plan(50.0, 255, 2.0, K=4).T == 203
+
+
+@pytest.mark.parametrize("sigma,eps", [(10.0, 0.01), (30.0, 0.01), (80.0, 0.01), (30.0, 0.1),
+                                       (50.0, 1e-3)])
+def test_fitter_algorithm1_matches_oracle(sigma, eps):
+    """Algorithm 1: same K*, T* and error."""
+    R = 255
+    p = B.Plan(sigma, R, 5.0, eps=eps)
+    o = ofit.make_plan(sigma, R, eps=eps)
+    assert (p.K, p.T) == (o.K, o.T)
+    assert p.E <= eps
+    np.testing.assert_allclose(_phi_hat(p.c, p.T, R), _phi_hat(o.c, o.T, R), rtol=0, atol=1e-10)
+
+
+def test_fitter_roundoff_region_phi_hat_agrees():
+    """K = 16, sigma = 80: E is at FP64 round-off for many T; compare through phi_hat."""
+    R = 255
+    p = B.Plan(80.0, R, 5.0, K=16)
+    o = ofit.make_plan(80.0, R, K=16)
+    assert p.E < 1e-15 and o.E < 1e-15
+    np.testing.assert_allclose(_phi_hat(p.c, p.T, R), ofit.kernel_samples(80.0, R), rtol=0, atol=1e-9)
+
+
+def test_error_curve_matches_oracle_including_rank_deficient():
+    """E(K,T) from the C++ folded Householder reduction against NumPy lstsq on the full
+    (2R+1) x K system.  Rank-deficient T (K > T+1) must agree exactly up to round-off;
+    at large T the columns are ill-conditioned and two backward-stable solvers may differ
+    by about eps * cond(A) * ||b||^2."""
+    R, sigma = 255, 20.0
+    b = ofit.kernel_samples(sigma, R)
+    for T in (1, 2, 5, 40, 150, 700):
+        E = B.fbf_debug_error_curve(b, R, T, 10)
+        for K in range(1, 11):
+            Eo, _ = ofit.kernel_error(K, T, b, R)
+            A = ofit.design_matrix(K, T, R)
+            s = np.linalg.svd(A, compute_uv=False)
+            s = s[s > s[0] * 1e-12]
+            tol = 1e-10 * max(1.0, Eo) + 8 * np.finfo(float).eps * (s[0] / s[-1]) * float(b @ b)
+            assert abs(E[K - 1] - Eo) <= tol, (T, K, E[K - 1], Eo)
+
+
+def test_fixed_period_flag_is_T_equals_R():
+    """FBF model (Section III): T = R, only the least-squares step; matches the oracle."""
+    R = 255
+    p = B.Plan(40.0, R, 3.0, K=4, flags=B.FBF_FLAG_FIXED_PERIOD)
+    o = ofit.make_plan(40.0, R, K=4, T=R)
+    assert p.T == R
+    np.testing.assert_allclose(_phi_hat(p.c, p.T, R), _phi_hat(o.c, o.T, R), rtol=0, atol=1e-12)
+
+
+def test_non_gaussian_kernel_from_samples():
+    """Any range kernel (Sections I, IV): the exponential kernel exp(-|t|/s)."""
+    R, s = 255, 25.0
+    kern = lambda t: np.exp(-np.abs(t) / s)  # noqa: E731
+    b = kern(np.arange(-R, R + 1))
+    p = B.Plan(None, R, 3.0, K=10, samples=b)
+    o = ofit.make_plan(None, R, K=10, kernel=kern)
+    assert p.T == o.T
+    np.testing.assert_allclose(_phi_hat(p.c, p.T, R), _phi_hat(o.c, o.T, R), rtol=0, atol=1e-10)
+
+
+@pytest.mark.parametrize("args,code", [
+    (dict(sigma=0.0, R=255, theta=3.0, K=4), B.FBF_EINVAL),
+    (dict(sigma=-1.0, R=255, theta=3.0, K=4), B.FBF_EINVAL),
+    (dict(sigma=30.0, R=0, theta=3.0, K=4), B.FBF_EINVAL),
+    (dict(sigma=30.0, R=255, theta=0.0, K=4), B.FBF_EINVAL),
+    (dict(sigma=30.0, R=255, theta=3.0, K=0, eps=0.0), B.FBF_EINVAL),
+    (dict(sigma=30.0, R=255, theta=3.0, K=-2), B.FBF_EINVAL),
+    (dict(sigma=30.0, R=255, theta=3.0, K=4, precision=99), B.FBF_EINVAL),
+    (dict(sigma=30.0, R=255, theta=3.0, K=4, flags=1 << 20), B.FBF_EINVAL),
+    (dict(sigma=30.0, R=255, theta=17.0, K=4), B.FBF_EUNSUPPORTED),
+    (dict(sigma=30.0, R=255, theta=3.0, K=B.FBF_MAX_K + 1), B.FBF_EUNSUPPORTED),
+])
+def test_plan_rejects_bad_arguments(args, code):
+    with pytest.raises(B.FbfError) as ei:
+        B.fbf_plan(**args)
+    assert ei.value.code == code
+    assert B.fbf_last_error()
+
+
+def test_filter_rejects_bad_arguments_without_touching_the_device():
+    p = B.Plan(30.0, 255, 3.0, K=4)
+    cases = [
+        (dict(d_in=0, d_out=1 << 20, H=4, W=4, pitch_elems=4), B.FBF_EINVAL),
+        (dict(d_in=1 << 20, d_out=0, H=4, W=4, pitch_elems=4), B.FBF_EINVAL),
+        (dict(d_in=1 << 20, d_out=1 << 24, H=0, W=4, pitch_elems=4), B.FBF_EINVAL),
+        (dict(d_in=1 << 20, d_out=1 << 24, H=4, W=-1, pitch_elems=4), B.FBF_EINVAL),
+        (dict(d_in=1 << 20, d_out=1 << 24, H=4, W=8, pitch_elems=4), B.FBF_EINVAL),
+        (dict(d_in=1 << 20, d_out=(1 << 20) + 16, H=4, W=4, pitch_elems=4), B.FBF_EINVAL),
+    ]
+    for kw, code in cases:
+        with pytest.raises(B.FbfError) as ei:
+            B.fbf_filter(p.handle, **kw)
+        assert ei.value.code == code
+    with pytest.raises(B.FbfError):
+        B.fbf_filter(0, 1 << 20, 1 << 24, 4, 4, 4)
+
+
+def test_plan_info_null_plan():
+    with pytest.raises(B.FbfError) as ei:
+        B.fbf_plan_info(0)
+    assert ei.value.code == B.FBF_EINVAL
