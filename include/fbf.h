@@ -119,6 +119,31 @@ int fbf_plan_destroy(fbf_plan_t plan);
 int fbf_filter(fbf_plan_t plan, const float* d_in, float* d_out, int H, int W,
                size_t pitch_elems, void* cuda_stream);
 
+/*
+ * fbf_filter_noalloc -- fbf_filter for callers that cannot allocate device memory while
+ * they filter (the paper has no counterpart; this is a deployment aid).  Examples: a
+ * framework whose caching allocator already holds nearly all of the GPU's memory, or a
+ * latency-bound serving loop in which cudaMalloc/cudaFree, which may synchronise the
+ * whole device, are not acceptable.  fbf_filter keeps a per-stream scratch workspace
+ * that it grows with cudaMalloc; this entry point instead takes its scratch (tile
+ * counters and partial sums) from one fixed device array of FBF_NOALLOC_SCRATCH_BYTES
+ * compiled into the library, which every GPU that loads the library holds until exit.
+ * It calls no cudaMalloc, cudaFree or allocating library routine.
+ *
+ * Arguments, layout and results are those of fbf_filter (FBF_FP32 plans only, else
+ * FBF_EUNSUPPORTED).  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before any
+ * stream capture.  Each call clears the counters it uses on `cuda_stream` before the
+ * kernel runs.  All calls share the one array: calls whose work overlaps on the GPU
+ * (different streams, or several host threads) race and must be serialised by the caller.
+ * Limit: the image may need at most 262144 tiles of 32 columns by 64 to 128 rows
+ * (about 2^28 pixels, e.g. 16384 x 16384); larger images are rejected with
+ * FBF_EUNSUPPORTED before any device work.
+ */
+#define FBF_NOALLOC_SCRATCH_BYTES (16u << 20)
+int fbf_filter_noalloc(fbf_plan_t plan, const float* d_in, float* d_out, int H, int W,
+                       size_t pitch_elems, void* cuda_stream);
+
 /* fbf_last_error -- message for the last failing call on this thread ("" if none). */
 const char* fbf_last_error(void);
 

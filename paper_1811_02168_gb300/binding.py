@@ -51,6 +51,8 @@ SIGNATURES = {
     "fbf_plan_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "fbf_filter": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                   ctypes.c_int, ctypes.c_size_t, ctypes.c_void_p]),
+    "fbf_filter_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                          ctypes.c_int, ctypes.c_size_t, ctypes.c_void_p]),
     "fbf_last_error": (ctypes.c_char_p, []),
     "fbf_version": (ctypes.c_char_p, []),
     "fbf_debug_error_curve": (ctypes.c_int, [_c_double_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -121,6 +123,11 @@ def fbf_plan_destroy(plan: int) -> None:
 def fbf_filter(plan: int, d_in: int, d_out: int, H: int, W: int, pitch_elems: int,
                stream: int = 0) -> None:
     _check(lib().fbf_filter(plan, d_in, d_out, H, W, pitch_elems, stream), "fbf_filter")
+
+
+def fbf_filter_noalloc(plan: int, d_in: int, d_out: int, H: int, W: int, pitch_elems: int,
+                       stream: int = 0) -> None:
+    _check(lib().fbf_filter_noalloc(plan, d_in, d_out, H, W, pitch_elems, stream), "fbf_filter_noalloc")
 
 
 def fbf_last_error() -> str:

@@ -158,6 +158,21 @@ int fbf_filter(fbf_plan_t plan, const float* d_in, float* d_out, int H, int W,
   }
 }
 
+int fbf_filter_noalloc(fbf_plan_t plan, const float* d_in, float* d_out, int H, int W,
+                       size_t pitch_elems, void* cuda_stream) {
+  if (!plan) return fbf::set_error(FBF_EINVAL, "fbf_filter_noalloc: plan is NULL");
+  if (!d_in || !d_out) return fbf::set_error(FBF_EINVAL, "fbf_filter_noalloc: NULL image pointer");
+  if (H < 1 || W < 1) return fbf::set_error(FBF_EINVAL, "fbf_filter_noalloc: H and W must be >= 1");
+  if (pitch_elems < (size_t)W) return fbf::set_error(FBF_EINVAL, "fbf_filter_noalloc: pitch < W");
+  const size_t span = ((size_t)(H - 1) * pitch_elems + (size_t)W) * sizeof(float);
+  const char* a = (const char*)d_in;
+  const char* o = (const char*)d_out;
+  if (a < o + span && o < a + span) return fbf::set_error(FBF_EINVAL, "fbf_filter_noalloc: in and out overlap");
+  if (plan->p.precision != FBF_FP32)
+    return fbf::set_error(FBF_EUNSUPPORTED, "fbf_filter_noalloc: only the FBF_FP32 form");
+  return fbf::launch_fp32_noalloc(plan->p.dp, d_in, d_out, H, W, pitch_elems, cuda_stream);
+}
+
 const char* fbf_last_error(void) { return fbf::g_last_error.c_str(); }
 
 const char* fbf_version(void) { return "fbf-gb300 0.1"; }

@@ -477,4 +477,117 @@ int launch_fp32(const DeviceParams& dp, const float* in, float* out, int H, int 
   return set_error(FBF_EUNSUPPORTED, "fbf_filter: radius too large");
 }
 
+// ---- allocation-free variant --------------------------------------------------------------
+// Some callers cannot allocate device memory while they filter: a framework whose caching
+// allocator already owns (nearly) all of the GPU's memory, or a latency-bound serving loop
+// in which a cudaMalloc/cudaFree -- which may synchronise the whole device -- is not
+// acceptable.  For them the FP32 kernel can take its scratch (tile counters and split-tile
+// partial sums) from this fixed, file-scope device array instead of the per-stream
+// workspace.  Every GPU that loads the library holds the array until the process exits.
+// Its address is looked up once per device (cudaGetSymbolAddress, with that device
+// current) by the first call on that device.  All calls share the array: calls whose
+// work overlaps on the GPU race on it.
+namespace {
+
+constexpr size_t kNoAllocCounterBytes = size_t(1) << 20;              // 262144 tile counters
+constexpr size_t kNoAllocPartialBytes = size_t(FBF_NOALLOC_SCRATCH_BYTES) - kNoAllocCounterBytes;
+static_assert(FBF_NOALLOC_SCRATCH_BYTES > (1 << 20), "scratch must hold the counters");
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[FBF_NOALLOC_SCRATCH_BYTES];
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[64] = {nullptr};
+
+// Host code must not use g_noalloc_scratch directly: in host code it names a host-side
+// stand-in, not device memory.  This returns the device address for the current device.
+int noalloc_scratch(int dev, void** out) {
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess || ptr == nullptr)
+      return set_error(FBF_ECUDA, std::string("fbf_filter_noalloc: cudaGetSymbolAddress: ") +
+                                      cudaGetErrorString(e));
+    g_noalloc_ptr[dev] = ptr;
+  }
+  *out = g_noalloc_ptr[dev];
+  return FBF_OK;
+}
+
+template <int RAD, int TY, int NT, int NY>
+int launch_cfg_noalloc(const DeviceParams& dp, const float* in, float* out, int H, int W,
+                       size_t pitch, cudaStream_t st) {
+  using C = Cfg<RAD, TY, NT, NY>;
+  static int occ[64] = {0};
+  static int sms[64] = {0};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return set_error(FBF_ECUDA, std::string("fbf_filter_noalloc: ") + cudaGetErrorString(e));
+  if (dev < 0 || dev >= 64) return set_error(FBF_EUNSUPPORTED, "fbf_filter_noalloc: device index >= 64");
+  Sched sc{};
+  sc.tiles_x = (W + TX - 1) / TX;
+  sc.tiles_y = (H + TY - 1) / TY;
+  sc.K = dp.K;
+  sc.wtile = 2 * dp.K - 1;
+  const long long tiles = (long long)sc.tiles_x * sc.tiles_y;
+  if ((size_t)tiles * sizeof(int) > kNoAllocCounterBytes)
+    return set_error(FBF_EUNSUPPORTED,
+                     "fbf_filter_noalloc: image needs " + std::to_string(tiles) + " tiles; the fixed "
+                     "scratch holds counters for " + std::to_string(kNoAllocCounterBytes / sizeof(int)));
+  void* base = nullptr;
+  int rc = noalloc_scratch(dev, &base);
+  if (rc != FBF_OK) return rc;
+  if (!occ[dev]) {
+    e = cudaFuncSetAttribute(fbf_fp32_kernel<RAD, TY, NT, NY>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM_BYTES);
+    if (e != cudaSuccess) return set_error(FBF_ECUDA, std::string("fbf_filter_noalloc: ") + cudaGetErrorString(e));
+    int n = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fbf_fp32_kernel<RAD, TY, NT, NY>, NT,
+                                                      C::SMEM_BYTES);
+    if (e != cudaSuccess || n < 1) return set_error(FBF_ECUDA, "fbf_filter_noalloc: kernel does not fit on an SM");
+    int s = 0;
+    cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev);
+    sms[dev] = s;
+    occ[dev] = n;
+  }
+  DeviceParams p = dp;
+  float g[2 * FBF_MAX_RADIUS + 1];
+  for (int i = 0; i <= 2 * RAD; ++i) {
+    const int d = i - (RAD - dp.r);
+    g[i] = (d >= 0 && d <= 2 * dp.r) ? dp.g[d] : 0.f;
+  }
+  for (int i = 0; i <= 2 * RAD; ++i) p.g[i] = g[i];
+  p.r = RAD;
+  sc.wtot = tiles * sc.wtile;
+  long long G = (long long)sms[dev] * occ[dev];
+  const long long per_cta = 2LL * 2 * NY * NT * (long long)sizeof(float);
+  if (G > (long long)(kNoAllocPartialBytes / per_cta)) G = (long long)(kNoAllocPartialBytes / per_cta);
+  if (G > sc.wtot) G = sc.wtot;
+  sc.counter = reinterpret_cast<int*>(base);
+  sc.partial = reinterpret_cast<float*>(static_cast<unsigned char*>(base) + kNoAllocCounterBytes);
+  // counters must start at zero; the array keeps whatever the previous call left
+  e = cudaMemsetAsync(sc.counter, 0, (size_t)tiles * sizeof(int), st);
+  if (e != cudaSuccess) return set_error(FBF_ECUDA, std::string("fbf_filter_noalloc: ") + cudaGetErrorString(e));
+  fbf_fp32_kernel<RAD, TY, NT, NY><<<(unsigned)G, NT, C::SMEM_BYTES, st>>>(p, in, out, H, W, (long)pitch, sc);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return set_error(FBF_ECUDA, std::string("fbf_filter_noalloc: launch: ") + cudaGetErrorString(e));
+  return FBF_OK;
+}
+
+}  // namespace
+
+int launch_fp32_noalloc(const DeviceParams& dp, const float* in, float* out, int H, int W,
+                        size_t pitch, void* stream) {
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int r = dp.r;
+  if (r <= 3) return launch_cfg_noalloc<3, 112, 512, 7>(dp, in, out, H, W, pitch, st);
+  if (r <= 6) return launch_cfg_noalloc<6, 112, 512, 7>(dp, in, out, H, W, pitch, st);
+  if (r <= 9) return launch_cfg_noalloc<9, 96, 512, 6>(dp, in, out, H, W, pitch, st);
+  if (r <= 15) return launch_cfg_noalloc<15, 96, 512, 6>(dp, in, out, H, W, pitch, st);
+  if (r <= 24) return launch_cfg_noalloc<24, 128, 256, 16>(dp, in, out, H, W, pitch, st);
+  if (r <= 30) return launch_cfg_noalloc<30, 128, 256, 16>(dp, in, out, H, W, pitch, st);
+  if (r <= 48) return launch_cfg_noalloc<48, 64, 128, 16>(dp, in, out, H, W, pitch, st);
+  return set_error(FBF_EUNSUPPORTED, "fbf_filter_noalloc: radius too large");
+}
+
 }  // namespace fbf

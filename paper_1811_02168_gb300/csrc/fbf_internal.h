@@ -59,5 +59,8 @@ void clear_error();
 // FP32 fused kernel launcher (fbf_fp32.cu).
 int launch_fp32(const DeviceParams& dp, const float* in, float* out, int H, int W,
                 size_t pitch, void* stream);
+// Same kernel, scratch from a fixed device array instead of the per-stream workspace.
+int launch_fp32_noalloc(const DeviceParams& dp, const float* in, float* out, int H, int W,
+                        size_t pitch, void* stream);
 
 }  // namespace fbf
