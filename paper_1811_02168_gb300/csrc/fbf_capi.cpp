@@ -73,6 +73,17 @@ int build_plan(fbf_plan_t* out, const double* b, int R, double theta, int K, dou
   d.nu = (float)(2.0 * M_PI / (double)d.P);
   d.invP = (float)(1.0 / (double)d.P);
   d.center = (float)(0.5 * (double)R);
+  d.R = R;
+  for (int a = 0; a * fbf::kTrigLo < d.P && a < fbf::kTrigHi; ++a) {
+    const double ang = 2.0 * M_PI * (double)(a * fbf::kTrigLo) / (double)d.P;
+    d.ta[2 * a] = (float)std::cos(ang);
+    d.ta[2 * a + 1] = (float)std::sin(ang);
+  }
+  for (int b = 0; b < fbf::kTrigLo; ++b) {
+    const double ang = 2.0 * M_PI * (double)b / (double)d.P;
+    d.tb[2 * b] = (float)std::cos(ang);
+    d.tb[2 * b + 1] = (float)std::sin(ang);
+  }
   for (int k = 0; k < d.K; ++k) d.c[k] = (float)p.fit.c[k];
   double gs = 0;
   for (int i = -r; i <= r; ++i) gs += std::exp(-(double)i * i / (2.0 * theta * theta));

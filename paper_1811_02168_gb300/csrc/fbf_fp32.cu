@@ -48,6 +48,7 @@ namespace {
 constexpr int TX = 32;                 // tile width
 constexpr int NXH = 8;                 // x outputs per lane in the x pass
 constexpr float kOutside = -3.0e38f;   // marks halo pixels outside the image
+constexpr int TABN = 256;              // per-term (cos, sin) table over integer intensities
 
 template <int RAD, int TY, int NT, int NY>
 struct Cfg {
@@ -64,7 +65,7 @@ struct Cfg {
   static constexpr int CPS0 = HROWS_P * HS2;
   static constexpr int CPS = CPS0 + ((4 - CPS0 % 16) + 16) % 16;  // pair stride, == 4 (mod 16)
   static constexpr size_t SMEM_BYTES =
-      (size_t)(NW * STAGE_F2 + 2 * CPS) * 8 + (size_t)HROWS_P * FHS * 4 + 16;
+      (size_t)(NW * STAGE_F2 + 2 * CPS + 2 * TABN) * 8 + (size_t)HROWS_P * FHS * 4 + 16;
   static_assert(TX * TY == NT * NY, "y-pass mapping: one column of NY pixels per thread");
   static_assert(TY % NY == 0 && (TY / NY) * 32 == NT, "y-pass mapping");
   static_assert(SMEM_BYTES <= 232448, "shared memory per CTA exceeds 227 KB");
@@ -91,16 +92,39 @@ __device__ __forceinline__ long long first_term_at(long long s, int K, int wtile
   return t * K + k;
 }
 
-// (cos, sin)(k nu v).  For integer v the angle is reduced exactly: x = k v is an integer
-// (exact in FP32 below 2^24) and n = x - P rint(x / P) is an exact integer in [-P/2, P/2]
-// (a rounding of x / P next to a half-integer only swaps +P/2 and -P/2), so the angle
-// n nu lies in [-pi, pi], where the fast hardware sine/cosine is accurate.
-__device__ __forceinline__ float2 term_cs(float kf, float v, const DeviceParams& p) {
+// (cos, sin)(k nu v) for any v: reduce x = k v by the period (n = x - P rint(x/P) lies in
+// [-P/2, P/2]), then the accurate sincospi.  Used for tiles whose values are not all
+// integers in [0, min(R, TABN-1)].
+__device__ __forceinline__ float2 term_cs_any(float kf, float v, const DeviceParams& p) {
   const float x = kf * v;
   const float n = fmaf(-rintf(x * p.invP), (float)p.P, x);
   float s, c;
-  __sincosf(n * p.nu, &s, &c);
+  sincospif(n * (2.0f * p.invP), &s, &c);
   return make_float2(c, s);
+}
+
+// Table of (cos, sin)(k nu v) for integer v = 0..TABN-1: the phase index n = (k v) mod P
+// is exact in integers and exp(i 2 pi n / P) is the product of the plan's two host-rounded
+// tables (n = 128 a + b), so every entry is within a few ulp of the exact value.
+template <int NT>
+__device__ __forceinline__ void build_term_table(const DeviceParams& p, int k, float2* dst2) {
+  float* dst = reinterpret_cast<float*>(dst2);   // [0, TABN): cos, [TABN, 2 TABN): sin
+  for (int v = threadIdx.x; v < TABN; v += NT) {
+    const int n = (k * v) % p.P;
+    const int a = n >> 7, b = n & (kTrigLo - 1);
+    const float ca = p.ta[2 * a], sa = p.ta[2 * a + 1];
+    const float cb = p.tb[2 * b], sb = p.tb[2 * b + 1];
+    dst[v] = fmaf(ca, cb, -sa * sb);
+    dst[TABN + v] = fmaf(sa, cb, ca * sb);
+  }
+}
+
+// table lookup for an integer value 0 <= v < TABN: the index is read from the float's
+// mantissa (v + 2^23 has v in its low bits), which keeps the conversion off the XU pipe
+__device__ __forceinline__ float2 tab_lookup(const float2* tab2, float v) {
+  const float* tab = reinterpret_cast<const float*>(tab2);
+  const unsigned i = __float_as_uint(v + 8388608.0f) & (TABN - 1);
+  return make_float2(tab[i], tab[TABN + i]);
 }
 
 // tap d of 0..2*RAD, read through the symmetric half so only RAD+1 registers are live
@@ -149,7 +173,8 @@ fbf_fp32_kernel(const __grid_constant__ DeviceParams p, const float* __restrict_
   const int warp = tid >> 5;
   float2* stage = smem2 + warp * C::STAGE_F2;
   float2* hbuf = smem2 + C::NW * C::STAGE_F2;
-  float* fh = reinterpret_cast<float*>(hbuf + 2 * C::CPS);
+  float2* tabs = hbuf + 2 * C::CPS;                    // two term tables (double buffer)
+  float* fh = reinterpret_cast<float*>(tabs + 2 * TABN);
   __shared__ int s_last;
 
   const int K = sc.K;
@@ -179,18 +204,28 @@ fbf_fp32_kernel(const __grid_constant__ DeviceParams p, const float* __restrict_
     const int ty0 = (int)(t / sc.tiles_x) * TY;
 
     // f of the tile plus halo (rows padded to whole x-pass rounds); kOutside marks
-    // pixels outside the image
+    // pixels outside the image.  The tile uses the term tables when all its values are
+    // integers in [0, min(R, TABN-1)] (8-bit images), else the sincospi path.
+    const float vmax = (float)min(p.R, TABN - 1);
+    int ok = 1;
     for (int i = tid; i < C::HROWS_P * C::TXH; i += NT) {
       const int row = i / C::TXH, xx = i - row * C::TXH;
       const int gy = ty0 - RAD + row, gx = tx0 - RAD + xx;
-      fh[row * C::FHS + xx] = (row < C::HROWS && gy >= 0 && gy < H && gx >= 0 && gx < W)
-                                  ? __ldg(in + (long)gy * pitch + gx)
-                                  : kOutside;
+      float v = kOutside;
+      if (row < C::HROWS && gy >= 0 && gy < H && gx >= 0 && gx < W) {
+        v = __ldg(in + (long)gy * pitch + gx);
+        ok &= (v == rintf(v)) & (v >= 0.f) & (v <= vmax);
+      }
+      fh[row * C::FHS + xx] = v;
     }
     // every halo pixel inside the image: generation needs no masking
     const bool interior = tx0 - RAD >= 0 && ty0 - RAD >= 0 && tx0 + TX + RAD <= W &&
                           ty0 + TY + RAD <= H;
-    __syncthreads();
+    const bool tile_int = __syncthreads_and(ok) != 0;
+    if (tile_int && kb >= 1) {
+      build_term_table<NT>(p, kb, tabs + (kb & 1) * TABN);
+      __syncthreads();
+    }
 
     float2 num2[NY], den2[NY];
 #pragma unroll
@@ -219,15 +254,31 @@ fbf_fp32_kernel(const __grid_constant__ DeviceParams p, const float* __restrict_
         }
       } else {
         // ---- term k >= 1: pairs (C, S) and (f'C, f'S); four halo rows per iteration --
+        const float2* tab = tabs + (k & 1) * TABN;
         for (int rb = warp * 4; rb < C::HROWS_P; rb += C::NW * 4) {
-          if (interior) {
+          if (tile_int && interior) {
 #pragma unroll
             for (int r4 = 0; r4 < 4; ++r4) {
 #pragma unroll
               for (int xx = lane; xx < C::TXH; xx += 32) {
                 const float v = fh[(rb + r4) * C::FHS + xx];
-                const float2 cs = term_cs(kf, v, p);
+                const float2 cs = tab_lookup(tab, v);
                 const float fm = v - m;
+                stage[(r4 * 2) * C::SWP + xx] = cs;
+                stage[(r4 * 2 + 1) * C::SWP + xx] = make_float2(fm * cs.x, fm * cs.y);
+              }
+            }
+          } else if (tile_int) {
+#pragma unroll
+            for (int r4 = 0; r4 < 4; ++r4) {
+#pragma unroll
+              for (int xx = lane; xx < C::TXH; xx += 32) {
+                const float v = fh[(rb + r4) * C::FHS + xx];
+                const bool in_img = v > kOutside;
+                float2 cs = tab_lookup(tab, in_img ? v : 0.f);
+                cs.x = in_img ? cs.x : 0.f;
+                cs.y = in_img ? cs.y : 0.f;
+                const float fm = in_img ? v - m : 0.f;
                 stage[(r4 * 2) * C::SWP + xx] = cs;
                 stage[(r4 * 2 + 1) * C::SWP + xx] = make_float2(fm * cs.x, fm * cs.y);
               }
@@ -239,7 +290,7 @@ fbf_fp32_kernel(const __grid_constant__ DeviceParams p, const float* __restrict_
               for (int xx = lane; xx < C::TXH; xx += 32) {
                 const float v = fh[(rb + r4) * C::FHS + xx];
                 const bool in_img = v > kOutside;
-                float2 cs = term_cs(kf, in_img ? v : 0.f, p);
+                float2 cs = term_cs_any(kf, in_img ? v : 0.f, p);
                 cs.x = in_img ? cs.x : 0.f;
                 cs.y = in_img ? cs.y : 0.f;
                 const float fm = in_img ? v - m : 0.f;
@@ -255,16 +306,20 @@ fbf_fp32_kernel(const __grid_constant__ DeviceParams p, const float* __restrict_
         }
       }
       __syncthreads();
+      // the next term's table goes to the other buffer while this term's is still read
+      if (tile_int && k + 1 < ke) build_term_table<NT>(p, k + 1, tabs + ((k + 1) & 1) * TABN);
 
       // ---- y pass for own pixels, folded into num/den ---------------------------------
       const int ncp = (k == 0) ? 1 : 2;
       float2 w[NY];
       if (k != 0) {
         const float ck = p.c[k];
+        const float2* tab = tabs + (k & 1) * TABN;
 #pragma unroll
         for (int a = 0; a < NY; ++a) {
           const float v = fh[(oy + a + RAD) * C::FHS + ox + RAD];
-          const float2 cs = term_cs(kf, v, p);
+          const bool in_img = v > kOutside;   // false only for pixels past the image edge
+          const float2 cs = tile_int ? tab_lookup(tab, in_img ? v : 0.f) : term_cs_any(kf, v, p);
           w[a] = make_float2(ck * cs.x, ck * cs.y);
         }
       }

@@ -31,17 +31,24 @@ void kernel_error_curve(const double* b, int R, int T, int Kc, double* E_out);
 // ---- device parameters ----------------------------------------------------------------
 // Everything a filter kernel needs, passed by value at launch (constant bank), so plans
 // own no device memory.
+// Unit-circle tables: e(n) = exp(i 2 pi n / P) for integer n = 128 a + b is the product
+// ta[a] * tb[b] of two tables rounded from double on the host (error ~2 ulp).
+constexpr int kTrigLo = 128;                                        // tb entries
+constexpr int kTrigHi = (FBF_MAX_PERIOD + kTrigLo - 1) / kTrigLo;  // ta entries
+
 struct DeviceParams {
   int K;                        // cosine terms
   int P;                        // period 2T+1
   int r;                        // spatial radius
-  int pad_;
+  int R;                        // intensity range [0, R]
   float nu;                     // 2 pi / P
   float invP;                   // 1 / P
   float center;                 // m: f-channels carry (f - m); m is added back at the end
-  float pad2_;
+  float pad_;
   float c[FBF_MAX_K];           // c_k (eq. 3)
   float g[2 * FBF_MAX_RADIUS + 1];  // g[d] = exp(-(d-r)^2/(2 theta^2)) / sum, d = 0..2r
+  float ta[2 * kTrigHi];        // (cos, sin)(2 pi 128 a / P), a = 0..P/128
+  float tb[2 * kTrigLo];        // (cos, sin)(2 pi b / P),     b = 0..127
 };
 
 struct Plan {

@@ -195,3 +195,27 @@ def test_host_end_to_end_api(B):
     res = B.bilateral_filter(plan, torch.from_numpy(img))
     assert not res.is_cuda
     assert np.array_equal(res.numpy(), _gpu(B, plan, img))
+
+
+def test_non_integer_input_uses_the_general_phase_path(B):
+    """Values that are not integers (Section II treats integer intensities; the library
+    filters any float input with the same formula) against the oracle's cos(k nu f)."""
+    rng = np.random.default_rng(31)
+    img = (voronoi_image(150, 170, 12, 30.0, 10.0, seed=31) * 0.9 +
+           rng.uniform(0.0, 0.999, (150, 170))).astype(np.float32)
+    plan = B.Plan(20.0, 255, 3.0, K=8)
+    op = _oracle_plan(20.0, K=8)
+    ref = ofl.fourier_bf(img.astype(np.float64), 3.0, op.c, op.T)
+    assert np.abs(_gpu(B, plan, img) - ref).max() <= TOL
+
+
+def test_ten_bit_image(B):
+    """R = 1023: intensities above the kernels' 256-entry term tables take the general
+    phase path; the fit covers Lambda = {-1023..1023}."""
+    R = 1023
+    img = np.rint(voronoi_image(96, 130, 10, 30.0, 10.0, seed=7) * 4.0).clip(0, R).astype(np.float32)
+    plan = B.Plan(120.0, R, 2.0, K=6)
+    op = ofit.make_plan(120.0, R, K=6)
+    assert (plan.K, plan.T) == (op.K, op.T)
+    ref = ofl.fourier_bf(img.astype(np.float64), 2.0, op.c, op.T)
+    assert np.abs(_gpu(B, plan, img) - ref).max() <= 4 * TOL   # scale: 4x the 8-bit range
