@@ -144,6 +144,65 @@ int fbf_filter(fbf_plan_t plan, const float* d_in, float* d_out, int H, int W,
 int fbf_filter_noalloc(fbf_plan_t plan, const float* d_in, float* d_out, int H, int W,
                        size_t pitch_elems, void* cuda_stream);
 
+/* ---- batched form (many images in one persistent launch) ------------------------- */
+typedef struct fbf_batch_s* fbf_batch_t;
+typedef uint64_t fbf_ticket_t;
+#define FBF_BATCH_AUTOTUNE 1   /* time each candidate tile configuration on first use */
+
+/*
+ * fbf_batch_create -- a batch context.  Images are queued with fbf_submit and filtered
+ * together by fbf_launch: per radius class (the kernel instantiation serving their
+ * r = ceil(3 theta)) one persistent stream-K launch runs over a device work-list of all
+ * (image, tile, cosine term) units, so small and large images share the GPU evenly.  Not
+ * in the paper (Section III filters one image at a time); the arithmetic per image is
+ * exactly fbf_filter's.  max_images (>= 1) bounds one launch; flags: FBF_BATCH_AUTOTUNE,
+ * under which the first launch of each (radius class, size bucket, K) times the candidate
+ * tile configurations and keeps the fastest (cached per process; appended to the file
+ * named by the environment variable FBF_TUNE_CACHE, read back by later processes).
+ * Host memory only until the first launch; device buffers are allocated at fbf_launch /
+ * fbf_batch_capture (never during fbf_batch_replay).  A batch's launches must be ordered
+ * (one stream, or caller-synchronised streams): they share the batch's scratch.
+ */
+int fbf_batch_create(fbf_batch_t* out, int max_images, int flags);
+
+/*
+ * fbf_submit -- queue one image (host-side only; nothing runs until fbf_launch).  Arguments
+ * as fbf_filter; FBF_FP32 plans only.  The plan must outlive the launch that uses it.
+ * *ticket (may be NULL) identifies the launch the image will belong to.
+ * Errors: FBF_EINVAL (bad arguments), FBF_EBUSY (max_images already queued),
+ * FBF_EUNSUPPORTED (other precision forms, radius beyond FBF_MAX_RADIUS).
+ */
+int fbf_submit(fbf_batch_t batch, fbf_plan_t plan, const float* d_in, float* d_out, int H, int W,
+               size_t pitch_elems, fbf_ticket_t* ticket);
+
+/* fbf_launch -- upload the work-list of the queued images and launch them on `cuda_stream`
+ * (asynchronous); the queue is emptied.  A no-op when nothing is queued. */
+int fbf_launch(fbf_batch_t batch, void* cuda_stream);
+
+/* fbf_batch_capture -- instead of launching, record the queued images' launch (work-list
+ * copy + kernels) as a CUDA graph owned by the batch, replacing any earlier one; the queue
+ * is emptied.  Tuning and allocation happen before the capture. */
+int fbf_batch_capture(fbf_batch_t batch, void* cuda_stream);
+
+/* fbf_batch_replay -- launch the captured graph on `cuda_stream` (same pointers and sizes,
+ * current image contents); *ticket (may be NULL) names this replay. */
+int fbf_batch_replay(fbf_batch_t batch, void* cuda_stream, fbf_ticket_t* ticket);
+
+/* fbf_poll -- non-blocking: *status = FBF_DONE when the ticket's launch has completed on
+ * the device, FBF_PENDING while it runs or is not launched yet.  A device error of the
+ * launch is returned as FBF_ECUDA. */
+int fbf_poll(fbf_batch_t batch, fbf_ticket_t ticket, int* status);
+
+/* fbf_wait -- block until the ticket's launch completes or timeout_s seconds pass
+ * (FBF_ETIMEDOUT; a ticket whose launch never happens times out). */
+int fbf_wait(fbf_batch_t batch, fbf_ticket_t ticket, double timeout_s);
+
+/* fbf_batch_pending -- number of queued, not yet launched images. */
+int fbf_batch_pending(fbf_batch_t batch, int* n);
+
+/* fbf_batch_destroy -- wait for the batch's launches, release its buffers (NULL ok). */
+int fbf_batch_destroy(fbf_batch_t batch);
+
 /* fbf_last_error -- message for the last failing call on this thread ("" if none). */
 const char* fbf_last_error(void);
 

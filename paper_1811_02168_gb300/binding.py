@@ -53,6 +53,17 @@ SIGNATURES = {
                                   ctypes.c_int, ctypes.c_size_t, ctypes.c_void_p]),
     "fbf_filter_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                           ctypes.c_int, ctypes.c_size_t, ctypes.c_void_p]),
+    "fbf_batch_create": (ctypes.c_int, [_c_void_pp, ctypes.c_int, ctypes.c_int]),
+    "fbf_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                  ctypes.c_int, ctypes.c_int, ctypes.c_size_t,
+                                  ctypes.POINTER(ctypes.c_uint64)]),
+    "fbf_launch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "fbf_batch_capture": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "fbf_batch_replay": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)]),
+    "fbf_poll": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, _c_int_p]),
+    "fbf_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_double]),
+    "fbf_batch_pending": (ctypes.c_int, [ctypes.c_void_p, _c_int_p]),
+    "fbf_batch_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "fbf_last_error": (ctypes.c_char_p, []),
     "fbf_version": (ctypes.c_char_p, []),
     "fbf_debug_error_curve": (ctypes.c_int, [_c_double_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -128,6 +139,55 @@ def fbf_filter(plan: int, d_in: int, d_out: int, H: int, W: int, pitch_elems: in
 def fbf_filter_noalloc(plan: int, d_in: int, d_out: int, H: int, W: int, pitch_elems: int,
                        stream: int = 0) -> None:
     _check(lib().fbf_filter_noalloc(plan, d_in, d_out, H, W, pitch_elems, stream), "fbf_filter_noalloc")
+
+
+FBF_BATCH_AUTOTUNE = 1
+
+
+def fbf_batch_create(max_images: int, flags: int = 0) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().fbf_batch_create(ctypes.byref(h), max_images, flags), "fbf_batch_create")
+    return h.value
+
+
+def fbf_submit(batch: int, plan: int, d_in: int, d_out: int, H: int, W: int, pitch_elems: int) -> int:
+    t = ctypes.c_uint64()
+    _check(lib().fbf_submit(batch, plan, d_in, d_out, H, W, pitch_elems, ctypes.byref(t)), "fbf_submit")
+    return t.value
+
+
+def fbf_launch(batch: int, stream: int = 0) -> None:
+    _check(lib().fbf_launch(batch, stream), "fbf_launch")
+
+
+def fbf_batch_capture(batch: int, stream: int = 0) -> None:
+    _check(lib().fbf_batch_capture(batch, stream), "fbf_batch_capture")
+
+
+def fbf_batch_replay(batch: int, stream: int = 0) -> int:
+    t = ctypes.c_uint64()
+    _check(lib().fbf_batch_replay(batch, stream, ctypes.byref(t)), "fbf_batch_replay")
+    return t.value
+
+
+def fbf_poll(batch: int, ticket: int) -> int:
+    st = ctypes.c_int()
+    _check(lib().fbf_poll(batch, ticket, ctypes.byref(st)), "fbf_poll")
+    return st.value
+
+
+def fbf_wait(batch: int, ticket: int, timeout_s: float) -> None:
+    _check(lib().fbf_wait(batch, ticket, timeout_s), "fbf_wait")
+
+
+def fbf_batch_pending(batch: int) -> int:
+    n = ctypes.c_int()
+    _check(lib().fbf_batch_pending(batch, ctypes.byref(n)), "fbf_batch_pending")
+    return n.value
+
+
+def fbf_batch_destroy(batch: int) -> None:
+    _check(lib().fbf_batch_destroy(batch), "fbf_batch_destroy")
 
 
 def fbf_last_error() -> str:
@@ -208,3 +268,55 @@ def bilateral_filter(plan: Plan, image, out=None, stream=None):
         st.synchronize()
         return res
     return dev_out
+
+
+class Batch:
+    """Owns an ``fbf_batch_t``: queue device images with ``submit``, run them with
+    ``launch`` (or ``capture`` once and ``replay``), and query tickets."""
+
+    def __init__(self, max_images: int, autotune: bool = False):
+        self.handle = fbf_batch_create(max_images, FBF_BATCH_AUTOTUNE if autotune else 0)
+        self._keep = []          # plans referenced by queued images stay alive
+
+    def submit(self, plan: Plan, x, y) -> int:
+        """x, y: 2-D float32 CUDA tensors with equal row strides."""
+        if x.stride(1) != 1 or y.stride(1) != 1 or x.stride(0) != y.stride(0):
+            raise ValueError("x and y need unit column stride and equal row strides")
+        self._keep.append(plan)
+        H, W = x.shape
+        return fbf_submit(self.handle, plan.handle, x.data_ptr(), y.data_ptr(), H, W, x.stride(0))
+
+    def launch(self, stream=None):
+        import torch
+        st = stream if stream is not None else torch.cuda.current_stream()
+        fbf_launch(self.handle, st.cuda_stream)
+
+    def capture(self, stream=None):
+        import torch
+        st = stream if stream is not None else torch.cuda.current_stream()
+        fbf_batch_capture(self.handle, st.cuda_stream)
+
+    def replay(self, stream=None) -> int:
+        import torch
+        st = stream if stream is not None else torch.cuda.current_stream()
+        return fbf_batch_replay(self.handle, st.cuda_stream)
+
+    def poll(self, ticket: int) -> int:
+        return fbf_poll(self.handle, ticket)
+
+    def wait(self, ticket: int, timeout_s: float = 60.0) -> None:
+        fbf_wait(self.handle, ticket, timeout_s)
+
+    def pending(self) -> int:
+        return fbf_batch_pending(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            fbf_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,680 @@
+// Batched Fourier bilateral filtering: many images in one persistent launch.
+//
+// Images are queued with fbf_submit (host only), then fbf_launch groups them by radius
+// class (the kernel instantiation that serves their r = ceil(3 theta)), uploads one device
+// work-list per class (per-image Work records and per-plan DeviceParams, one copy from a
+// pinned staging buffer) and starts one stream-K persistent kernel per class over the
+// concatenated (image, tile, term) sequence of the class.  An event recorded after the
+// launches marks the generation; tickets name a generation and fbf_poll / fbf_wait query
+// it.  fbf_batch_capture records the same work as a CUDA graph (copy + kernels) that
+// fbf_batch_replay relaunches with the same pointers and sizes.
+//
+// Autotuning (FBF_BATCH_AUTOTUNE): the first launch of each (radius class, total pixels
+// rounded to a power of two, longest K) key times every candidate tile configuration of the
+// class on the real work-list with CUDA events and keeps the fastest; the choice is cached
+// per device and, if FBF_TUNE_CACHE names a file, persisted there as "key config" lines.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstddef>
+#include <cstring>
+#include <map>
+#include <new>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "fbf_fp32_body.cuh"
+#include "fbf_internal.h"
+
+namespace fbf {
+namespace {
+
+using namespace fp32;
+
+// ---- kernel configurations per radius class --------------------------------------------
+struct ClassLaunch {
+  // launches the batched kernel of one configuration; returns FBF_OK or an error code
+  int (*launch)(const DeviceParams* dparams, const Work* dwork, int n, long long wtot,
+                float* partial, int* counter, cudaStream_t st, int dev);
+  // partial-sum bytes one launch of this configuration needs (per CTA slots) on dev
+  int (*partial_bytes)(int dev, size_t* out);
+  int TY;
+  const char* name;
+};
+
+template <int RAD, int TY, int NT, int NY>
+struct BatchCfg {
+  using C = Cfg<RAD, TY, NT, NY>;
+  static int sms[64], occ[64];
+  static int slots(int dev, int* G) {
+    if (!occ[dev]) {
+      cudaError_t e = cudaFuncSetAttribute(fbf_fp32_batch_kernel<RAD, TY, NT, NY>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM_BYTES);
+      if (e != cudaSuccess) return set_error(FBF_ECUDA, std::string("fbf_launch: ") + cudaGetErrorString(e));
+      int n = 0;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fbf_fp32_batch_kernel<RAD, TY, NT, NY>, NT,
+                                                        C::SMEM_BYTES);
+      if (e != cudaSuccess || n < 1) return set_error(FBF_ECUDA, "fbf_launch: kernel does not fit on an SM");
+      int s = 0;
+      cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev);
+      sms[dev] = s;
+      occ[dev] = n;
+    }
+    *G = sms[dev] * occ[dev];
+    return FBF_OK;
+  }
+  static int partial_bytes(int dev, size_t* out) {
+    int G = 0;
+    int rc = slots(dev, &G);
+    if (rc != FBF_OK) return rc;
+    *out = (size_t)G * 2 * 2 * NY * NT * sizeof(float);
+    return FBF_OK;
+  }
+  static int launch(const DeviceParams* dparams, const Work* dwork, int n, long long wtot,
+                    float* partial, int* counter, cudaStream_t st, int dev) {
+    int G = 0;
+    int rc = slots(dev, &G);
+    if (rc != FBF_OK) return rc;
+    long long g = G;
+    if (g > wtot) g = wtot;
+    Scratch sc{};
+    sc.wtot = wtot;
+    sc.partial = partial;
+    sc.counter = counter;
+    fbf_fp32_batch_kernel<RAD, TY, NT, NY><<<(unsigned)g, NT, C::SMEM_BYTES, st>>>(dparams, dwork, n, sc);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return set_error(FBF_ECUDA, std::string("fbf_launch: ") + cudaGetErrorString(e));
+    return FBF_OK;
+  }
+};
+template <int RAD, int TY, int NT, int NY> int BatchCfg<RAD, TY, NT, NY>::sms[64] = {0};
+template <int RAD, int TY, int NT, int NY> int BatchCfg<RAD, TY, NT, NY>::occ[64] = {0};
+
+template <int RAD, int TY, int NT, int NY>
+constexpr ClassLaunch cfg_entry(const char* name) {
+  return ClassLaunch{&BatchCfg<RAD, TY, NT, NY>::launch, &BatchCfg<RAD, TY, NT, NY>::partial_bytes, TY, name};
+}
+
+struct RadClass {
+  int rad;
+  std::vector<ClassLaunch> cands;   // first = default
+};
+
+const std::vector<RadClass>& classes() {
+  static const std::vector<RadClass> cls = {
+      {3, {cfg_entry<3, 112, 512, 7>("r3_ty112_nt512")}},
+      {6, {cfg_entry<6, 112, 512, 7>("r6_ty112_nt512"), cfg_entry<6, 128, 256, 16>("r6_ty128_nt256")}},
+      {9, {cfg_entry<9, 96, 512, 6>("r9_ty96_nt512")}},
+      {15, {cfg_entry<15, 96, 512, 6>("r15_ty96_nt512"), cfg_entry<15, 128, 256, 16>("r15_ty128_nt256")}},
+      {24, {cfg_entry<24, 128, 256, 16>("r24_ty128_nt256")}},
+      {30, {cfg_entry<30, 128, 256, 16>("r30_ty128_nt256"), cfg_entry<30, 96, 256, 12>("r30_ty96_nt256")}},
+      {48, {cfg_entry<48, 64, 128, 16>("r48_ty64_nt128")}},
+  };
+  return cls;
+}
+
+int class_of(int r) {
+  const auto& cls = classes();
+  for (size_t i = 0; i < cls.size(); ++i)
+    if (r <= cls[i].rad) return (int)i;
+  return -1;
+}
+
+DeviceParams padded(const DeviceParams& dp, int rad) {
+  DeviceParams p = dp;
+  float g[2 * FBF_MAX_RADIUS + 1];
+  for (int i = 0; i <= 2 * rad; ++i) {
+    const int d = i - (rad - dp.r);
+    g[i] = (d >= 0 && d <= 2 * dp.r) ? dp.g[d] : 0.f;
+  }
+  for (int i = 0; i <= 2 * rad; ++i) p.g[i] = g[i];
+  p.r = rad;
+  return p;
+}
+
+// ---- autotuner cache ----------------------------------------------------------------------
+std::mutex g_tune_mu;
+std::map<std::string, int> g_tune;   // key -> candidate index
+bool g_tune_loaded = false;
+
+std::string tune_key(int dev, int cls, long long pixels, int kmax) {
+  cudaDeviceProp prop{};
+  cudaGetDeviceProperties(&prop, dev);
+  int lg = 0;
+  while ((1LL << (lg + 1)) <= pixels) ++lg;
+  std::string name(prop.name);
+  for (auto& ch : name)
+    if (ch == ' ') ch = '_';
+  return name + "/r" + std::to_string(classes()[cls].rad) + "/px2^" + std::to_string(lg) + "/K" +
+         std::to_string(kmax);
+}
+
+void tune_load_locked() {
+  if (g_tune_loaded) return;
+  g_tune_loaded = true;
+  const char* path = std::getenv("FBF_TUNE_CACHE");
+  if (!path) return;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return;
+  char key[256], cfg[128];
+  while (std::fscanf(f, "%255s %127s", key, cfg) == 2) {
+    std::string k(key);
+    // find the class index from the key's radius and the candidate by name
+    for (size_t ci = 0; ci < classes().size(); ++ci)
+      for (size_t j = 0; j < classes()[ci].cands.size(); ++j)
+        if (std::string(classes()[ci].cands[j].name) == cfg) g_tune[k] = (int)j;
+  }
+  std::fclose(f);
+}
+
+void tune_store_locked(const std::string& key, const char* cfg) {
+  const char* path = std::getenv("FBF_TUNE_CACHE");
+  if (!path) return;
+  FILE* f = std::fopen(path, "a");
+  if (!f) return;
+  std::fprintf(f, "%s %s\n", key.c_str(), cfg);
+  std::fclose(f);
+}
+
+}  // namespace
+
+// ---- the batch object ------------------------------------------------------------------------
+struct Pending {
+  const Plan* plan;
+  const float* in;
+  float* out;
+  int H, W;
+  size_t pitch;
+};
+
+struct Generation {
+  unsigned long long id;
+  cudaEvent_t ev;
+};
+
+struct Batch {
+  int max_images = 0;
+  int flags = 0;
+  int dev = -1;
+  std::vector<Pending> pending;
+  unsigned long long next_gen = 1;       // generation the pending images will belong to
+  std::vector<Generation> gens;          // launched, not yet known complete
+  unsigned long long done_below = 1;     // every generation < done_below is complete
+  // work-list buffers: a ring for fbf_launch (a slot is rewritten only after the copy that
+  // read it has run) and one slot owned by the captured graph
+  static constexpr int kRing = 4;
+  struct ListBuf {
+    void* h = nullptr;                   // pinned staging
+    void* d = nullptr;
+    size_t cap = 0;
+    cudaEvent_t copied = nullptr;        // recorded after the copy out of h
+    bool pending = false;
+  };
+  ListBuf ring[kRing + 1];               // [kRing] belongs to the graph
+  int slot = 0;                          // slot in use by the current prepare/launch
+  unsigned long long launches = 0;
+  void* d_scratch = nullptr;
+  size_t counter_cap = 0, partial_cap = 0;
+  // graph
+  cudaGraphExec_t graph = nullptr;
+  cudaStream_t capture_stream = nullptr;
+  std::vector<cudaEvent_t> free_events;
+  std::mutex mu;
+};
+
+namespace {
+
+int ensure_device(Batch* b) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return set_error(FBF_ECUDA, std::string("fbf_launch: ") + cudaGetErrorString(e));
+  if (dev < 0 || dev >= 64) return set_error(FBF_EUNSUPPORTED, "fbf_launch: device index >= 64");
+  if (b->dev >= 0 && b->dev != dev) return set_error(FBF_EINVAL, "fbf_launch: batch used on another device");
+  b->dev = dev;
+  return FBF_OK;
+}
+
+struct ClassPlan {
+  int cls = -1;
+  int cand = 0;
+  std::vector<Work> works;
+  std::vector<DeviceParams> params;
+  long long wtot = 0, tiles = 0, pixels = 0;
+  int kmax = 0;
+  size_t params_off = 0, work_off = 0;    // offsets in the lists buffer
+};
+
+// group the pending images by radius class and lay out the device lists
+int build_lists(Batch* b, std::vector<ClassPlan>* out, size_t* bytes) {
+  std::map<int, ClassPlan> by;
+  for (const Pending& pd : b->pending) {
+    const int cls = class_of(pd.plan->r);
+    if (cls < 0) return set_error(FBF_EUNSUPPORTED, "fbf_launch: radius too large");
+    ClassPlan& cp = by[cls];
+    cp.cls = cls;
+    // one DeviceParams per distinct plan in the class
+    const DeviceParams q = padded(pd.plan->dp, classes()[cls].rad);
+    int pidx = -1;
+    for (size_t i = 0; i < cp.params.size() && pidx < 0; ++i)
+      if (std::memcmp(&q, &cp.params[i], sizeof(DeviceParams)) == 0) pidx = (int)i;
+    if (pidx < 0) {
+      cp.params.push_back(q);
+      pidx = (int)cp.params.size() - 1;
+    }
+    Work w{};
+    w.in = pd.in;
+    w.out = pd.out;
+    w.pitch = (long long)pd.pitch;
+    w.H = pd.H;
+    w.W = pd.W;
+    w.K = pd.plan->dp.K;
+    w.wtile = 2 * w.K - 1;
+    w.param_idx = pidx;
+    cp.works.push_back(w);
+    cp.pixels += (long long)pd.H * pd.W;
+    cp.kmax = std::max(cp.kmax, w.K);
+  }
+  size_t off = 0;
+  for (auto& kv : by) {
+    ClassPlan cp = kv.second;
+    cp.params_off = off;
+    off += ((cp.params.size() * sizeof(DeviceParams) + 255) / 256) * 256;
+    cp.work_off = off;
+    off += ((cp.works.size() * sizeof(Work) + 255) / 256) * 256;
+    out->push_back(cp);
+  }
+  *bytes = off;
+  return FBF_OK;
+}
+
+// tile geometry of a class plan for candidate `cand`
+void layout(ClassPlan& cp, int cand) {
+  const int TY = classes()[cp.cls].cands[cand].TY;
+  long long wst = 0, tiles = 0;
+  for (Work& w : cp.works) {
+    w.tiles_x = (w.W + TX - 1) / TX;
+    w.tiles_y = (w.H + TY - 1) / TY;
+    w.tiles = (long long)w.tiles_x * w.tiles_y;
+    w.wstart = wst;
+    w.counter_base = (int)tiles;
+    wst += w.tiles * w.wtile;
+    tiles += w.tiles;
+  }
+  cp.wtot = wst;
+  cp.tiles = tiles;
+  cp.cand = cand;
+}
+
+int ensure_buffers(Batch* b, size_t list_bytes, size_t counters, size_t partial) {
+  cudaError_t e;
+  Batch::ListBuf& lb = b->ring[b->slot];
+  if (lb.pending) {   // the copy that last read this slot must have run
+    e = cudaEventSynchronize(lb.copied);
+    if (e != cudaSuccess) return set_error(FBF_ECUDA, std::string("fbf_launch: ") + cudaGetErrorString(e));
+    lb.pending = false;
+  }
+  if (!lb.copied) {
+    e = cudaEventCreateWithFlags(&lb.copied, cudaEventDisableTiming);
+    if (e != cudaSuccess) return set_error(FBF_ECUDA, std::string("fbf_launch: ") + cudaGetErrorString(e));
+  }
+  if (lb.cap < list_bytes) {
+    if (lb.h) cudaFreeHost(lb.h);
+    if (lb.d) { cudaDeviceSynchronize(); cudaFree(lb.d); }
+    lb.h = lb.d = nullptr;
+    lb.cap = 0;
+    e = cudaMallocHost(&lb.h, list_bytes);
+    if (e != cudaSuccess) return set_error(FBF_ENOMEM, std::string("fbf_launch: ") + cudaGetErrorString(e));
+    e = cudaMalloc(&lb.d, list_bytes);
+    if (e != cudaSuccess) return set_error(FBF_ENOMEM, std::string("fbf_launch: ") + cudaGetErrorString(e));
+    lb.cap = list_bytes;
+  }
+  if (b->counter_cap < counters || b->partial_cap < partial) {
+    if (b->d_scratch) { cudaDeviceSynchronize(); cudaFree(b->d_scratch); }
+    b->d_scratch = nullptr;
+    const size_t cc = std::max(counters + counters / 2, (size_t)1024);
+    const size_t pc = partial + partial / 2;
+    const size_t cbytes = ((cc * sizeof(int) + 255) / 256) * 256;
+    e = cudaMalloc(&b->d_scratch, cbytes + pc);
+    if (e != cudaSuccess) return set_error(FBF_ENOMEM, std::string("fbf_launch: ") + cudaGetErrorString(e));
+    e = cudaMemset(b->d_scratch, 0, cbytes);   // counters start at zero; launches leave them at zero
+    if (e != cudaSuccess) return set_error(FBF_ECUDA, std::string("fbf_launch: ") + cudaGetErrorString(e));
+    b->counter_cap = cc;
+    b->partial_cap = pc;
+  }
+  return FBF_OK;
+}
+
+int* scratch_counters(Batch* b) { return reinterpret_cast<int*>(b->d_scratch); }
+float* scratch_partials(Batch* b) {
+  const size_t cbytes = ((b->counter_cap * sizeof(int) + 255) / 256) * 256;
+  return reinterpret_cast<float*>(static_cast<char*>(b->d_scratch) + cbytes);
+}
+
+void write_lists(Batch* b, const std::vector<ClassPlan>& cps) {
+  char* h = static_cast<char*>(b->ring[b->slot].h);
+  for (const ClassPlan& cp : cps) {
+    std::memcpy(h + cp.params_off, cp.params.data(), cp.params.size() * sizeof(DeviceParams));
+    std::memcpy(h + cp.work_off, cp.works.data(), cp.works.size() * sizeof(Work));
+  }
+}
+
+int launch_classes(Batch* b, const std::vector<ClassPlan>& cps, size_t list_bytes, cudaStream_t st,
+                   bool capturing) {
+  Batch::ListBuf& lb = b->ring[b->slot];
+  cudaError_t e = cudaMemcpyAsync(lb.d, lb.h, list_bytes, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return set_error(FBF_ECUDA, std::string("fbf_launch: ") + cudaGetErrorString(e));
+  if (!capturing) {
+    e = cudaEventRecord(lb.copied, st);
+    if (e != cudaSuccess) return set_error(FBF_ECUDA, std::string("fbf_launch: ") + cudaGetErrorString(e));
+    lb.pending = true;
+  }
+  char* d = static_cast<char*>(lb.d);
+  for (const ClassPlan& cp : cps) {
+    const ClassLaunch& cl = classes()[cp.cls].cands[cp.cand];
+    int rc = cl.launch(reinterpret_cast<const DeviceParams*>(d + cp.params_off),
+                       reinterpret_cast<const Work*>(d + cp.work_off), (int)cp.works.size(), cp.wtot,
+                       scratch_partials(b), scratch_counters(b), st, b->dev);
+    if (rc != FBF_OK) return rc;
+  }
+  return FBF_OK;
+}
+
+// choose a candidate per class (autotuned or default) and size the buffers
+int prepare(Batch* b, std::vector<ClassPlan>* cps, size_t* list_bytes, cudaStream_t st, bool allow_tune) {
+  int rc = build_lists(b, cps, list_bytes);
+  if (rc != FBF_OK) return rc;
+  size_t counters = 0, partial = 0;
+  for (ClassPlan& cp : *cps) {
+    const auto& cands = classes()[cp.cls].cands;
+    int choice = 0;
+    if ((b->flags & FBF_BATCH_AUTOTUNE) && cands.size() > 1) {
+      const std::string key = tune_key(b->dev, cp.cls, cp.pixels, cp.kmax);
+      int cached = -1;
+      {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        tune_load_locked();
+        auto it = g_tune.find(key);
+        if (it != g_tune.end() && it->second < (int)cands.size()) cached = it->second;
+      }
+      if (cached >= 0) {
+        choice = cached;
+      } else if (allow_tune) {
+        // time every candidate on this class's real work-list (outputs are rewritten later)
+        float best = 1e30f;
+        for (size_t j = 0; j < cands.size(); ++j) {
+          ClassPlan one = cp;
+          layout(one, (int)j);
+          size_t pb = 0;
+          rc = cands[j].partial_bytes(b->dev, &pb);
+          if (rc != FBF_OK) return rc;
+          rc = ensure_buffers(b, *list_bytes, (size_t)one.tiles, pb);
+          if (rc != FBF_OK) return rc;
+          std::vector<ClassPlan> v{one};
+          write_lists(b, v);
+          cudaEvent_t e0, e1;
+          cudaEventCreate(&e0);
+          cudaEventCreate(&e1);
+          float ms_best = 1e30f;
+          for (int rep = 0; rep < 3; ++rep) {
+            cudaEventRecord(e0, st);
+            rc = launch_classes(b, v, *list_bytes, st, false);
+            cudaEventRecord(e1, st);
+            if (rc != FBF_OK) break;
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) ms_best = std::min(ms_best, ms);
+          }
+          cudaEventDestroy(e0);
+          cudaEventDestroy(e1);
+          if (rc != FBF_OK) return rc;
+          if (ms_best < best) { best = ms_best; choice = (int)j; }
+        }
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune[key] = choice;
+        tune_store_locked(key, cands[choice].name);
+      }
+    }
+    layout(cp, choice);
+    size_t pb = 0;
+    rc = cands[choice].partial_bytes(b->dev, &pb);
+    if (rc != FBF_OK) return rc;
+    counters = std::max(counters, (size_t)cp.tiles);
+    partial = std::max(partial, pb);
+  }
+  rc = ensure_buffers(b, *list_bytes, counters, partial);
+  if (rc != FBF_OK) return rc;
+  write_lists(b, *cps);
+  return FBF_OK;
+}
+
+int record_generation(Batch* b, cudaStream_t st, unsigned long long* gen_out) {
+  cudaEvent_t ev;
+  if (!b->free_events.empty()) {
+    ev = b->free_events.back();
+    b->free_events.pop_back();
+  } else {
+    cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return set_error(FBF_ECUDA, std::string("fbf_launch: ") + cudaGetErrorString(e));
+  }
+  cudaError_t e = cudaEventRecord(ev, st);
+  if (e != cudaSuccess) return set_error(FBF_ECUDA, std::string("fbf_launch: ") + cudaGetErrorString(e));
+  const unsigned long long g = b->next_gen++;
+  b->gens.push_back({g, ev});
+  *gen_out = g;
+  // keep the outstanding list bounded: the oldest generations are waited for
+  while (b->gens.size() > 1024) {
+    cudaEventSynchronize(b->gens.front().ev);
+    b->free_events.push_back(b->gens.front().ev);
+    b->done_below = b->gens.front().id + 1;
+    b->gens.erase(b->gens.begin());
+  }
+  return FBF_OK;
+}
+
+// status of a generation: FBF_DONE, FBF_PENDING, or an error code
+int gen_status(Batch* b, unsigned long long g) {
+  if (g >= b->next_gen) return FBF_PENDING;   // not launched yet
+  if (g < b->done_below) return FBF_DONE;
+  // complete generations at the front are retired in order
+  while (!b->gens.empty()) {
+    cudaError_t e = cudaEventQuery(b->gens.front().ev);
+    if (e == cudaErrorNotReady) break;
+    if (e != cudaSuccess) return set_error(FBF_ECUDA, std::string("fbf_poll: ") + cudaGetErrorString(e));
+    b->done_below = b->gens.front().id + 1;
+    b->free_events.push_back(b->gens.front().ev);
+    b->gens.erase(b->gens.begin());
+  }
+  if (g < b->done_below) return FBF_DONE;
+  for (const Generation& gen : b->gens) {
+    if (gen.id == g) {
+      cudaError_t e = cudaEventQuery(gen.ev);
+      if (e == cudaSuccess) return FBF_DONE;
+      if (e == cudaErrorNotReady) return FBF_PENDING;
+      return set_error(FBF_ECUDA, std::string("fbf_poll: ") + cudaGetErrorString(e));
+    }
+  }
+  return FBF_DONE;
+}
+
+}  // namespace
+}  // namespace fbf
+
+struct fbf_batch_s {
+  fbf::Batch b;
+};
+
+extern "C" {
+
+int fbf_batch_create(fbf_batch_t* out, int max_images, int flags) {
+  if (!out) return fbf::set_error(FBF_EINVAL, "fbf_batch_create: out is NULL");
+  *out = nullptr;
+  if (max_images < 1) return fbf::set_error(FBF_EINVAL, "fbf_batch_create: max_images must be >= 1");
+  if (flags & ~FBF_BATCH_AUTOTUNE) return fbf::set_error(FBF_EINVAL, "fbf_batch_create: unknown flag");
+  fbf_batch_s* h = new (std::nothrow) fbf_batch_s();
+  if (!h) return fbf::set_error(FBF_ENOMEM, "fbf_batch_create: out of host memory");
+  h->b.max_images = max_images;
+  h->b.flags = flags;
+  *out = h;
+  return FBF_OK;
+}
+
+int fbf_submit(fbf_batch_t batch, fbf_plan_t plan, const float* d_in, float* d_out, int H, int W,
+               size_t pitch_elems, fbf_ticket_t* ticket) {
+  if (!batch || !plan) return fbf::set_error(FBF_EINVAL, "fbf_submit: NULL batch or plan");
+  if (!d_in || !d_out) return fbf::set_error(FBF_EINVAL, "fbf_submit: NULL image pointer");
+  if (H < 1 || W < 1) return fbf::set_error(FBF_EINVAL, "fbf_submit: H and W must be >= 1");
+  if (pitch_elems < (size_t)W) return fbf::set_error(FBF_EINVAL, "fbf_submit: pitch < W");
+  const fbf::Plan* p = fbf::plan_of(plan);
+  if (p->precision != FBF_FP32) return fbf::set_error(FBF_EUNSUPPORTED, "fbf_submit: only the FBF_FP32 form");
+  if (fbf::class_of(p->r) < 0) return fbf::set_error(FBF_EUNSUPPORTED, "fbf_submit: radius too large");
+  const size_t span = ((size_t)(H - 1) * pitch_elems + (size_t)W) * sizeof(float);
+  const char* a = (const char*)d_in;
+  const char* o = (const char*)d_out;
+  if (a < o + span && o < a + span) return fbf::set_error(FBF_EINVAL, "fbf_submit: in and out overlap");
+  fbf::Batch& b = batch->b;
+  std::lock_guard<std::mutex> lk(b.mu);
+  if ((int)b.pending.size() >= b.max_images) return fbf::set_error(FBF_EBUSY, "fbf_submit: batch is full");
+  b.pending.push_back({p, d_in, d_out, H, W, pitch_elems});
+  if (ticket) *ticket = (fbf_ticket_t)b.next_gen;
+  return FBF_OK;
+}
+
+int fbf_launch(fbf_batch_t batch, void* cuda_stream) {
+  if (!batch) return fbf::set_error(FBF_EINVAL, "fbf_launch: batch is NULL");
+  fbf::Batch& b = batch->b;
+  std::lock_guard<std::mutex> lk(b.mu);
+  if (b.pending.empty()) return FBF_OK;
+  int rc = fbf::ensure_device(&b);
+  if (rc != FBF_OK) return rc;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
+  b.slot = (int)(b.launches % fbf::Batch::kRing);
+  std::vector<fbf::ClassPlan> cps;
+  size_t list_bytes = 0;
+  rc = fbf::prepare(&b, &cps, &list_bytes, st, true);
+  if (rc != FBF_OK) return rc;
+  rc = fbf::launch_classes(&b, cps, list_bytes, st, false);
+  if (rc != FBF_OK) return rc;
+  unsigned long long g = 0;
+  rc = fbf::record_generation(&b, st, &g);
+  if (rc != FBF_OK) return rc;
+  ++b.launches;
+  b.pending.clear();
+  return FBF_OK;
+}
+
+int fbf_batch_capture(fbf_batch_t batch, void* cuda_stream) {
+  if (!batch) return fbf::set_error(FBF_EINVAL, "fbf_batch_capture: batch is NULL");
+  fbf::Batch& b = batch->b;
+  std::lock_guard<std::mutex> lk(b.mu);
+  if (b.pending.empty()) return fbf::set_error(FBF_EINVAL, "fbf_batch_capture: no submitted images");
+  int rc = fbf::ensure_device(&b);
+  if (rc != FBF_OK) return rc;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
+  b.slot = fbf::Batch::kRing;   // the graph owns this slot's staging and device lists
+  std::vector<fbf::ClassPlan> cps;
+  size_t list_bytes = 0;
+  rc = fbf::prepare(&b, &cps, &list_bytes, st, true);   // tuning and allocation happen here
+  if (rc != FBF_OK) return rc;
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fbf::set_error(FBF_ECUDA, std::string("fbf_batch_capture: ") + cudaGetErrorString(e));
+  // capture on the batch's own stream: the caller's may be the legacy default stream,
+  // which cannot be captured; the graph is later launched on any stream
+  if (!b.capture_stream) {
+    e = cudaStreamCreateWithFlags(&b.capture_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return fbf::set_error(FBF_ECUDA, std::string("fbf_batch_capture: ") + cudaGetErrorString(e));
+  }
+  cudaGraph_t graph = nullptr;
+  e = cudaStreamBeginCapture(b.capture_stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return fbf::set_error(FBF_ECUDA, std::string("fbf_batch_capture: ") + cudaGetErrorString(e));
+  rc = fbf::launch_classes(&b, cps, list_bytes, b.capture_stream, true);
+  e = cudaStreamEndCapture(b.capture_stream, &graph);
+  if (rc != FBF_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  if (e != cudaSuccess) return fbf::set_error(FBF_ECUDA, std::string("fbf_batch_capture: ") + cudaGetErrorString(e));
+  if (b.graph) cudaGraphExecDestroy(b.graph);
+  b.graph = nullptr;
+  e = cudaGraphInstantiate(&b.graph, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return fbf::set_error(FBF_ECUDA, std::string("fbf_batch_capture: ") + cudaGetErrorString(e));
+  b.pending.clear();
+  return FBF_OK;
+}
+
+int fbf_batch_replay(fbf_batch_t batch, void* cuda_stream, fbf_ticket_t* ticket) {
+  if (!batch) return fbf::set_error(FBF_EINVAL, "fbf_batch_replay: batch is NULL");
+  fbf::Batch& b = batch->b;
+  std::lock_guard<std::mutex> lk(b.mu);
+  if (!b.graph) return fbf::set_error(FBF_EINVAL, "fbf_batch_replay: nothing captured");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
+  cudaError_t e = cudaGraphLaunch(b.graph, st);
+  if (e != cudaSuccess) return fbf::set_error(FBF_ECUDA, std::string("fbf_batch_replay: ") + cudaGetErrorString(e));
+  unsigned long long g = 0;
+  int rc = fbf::record_generation(&b, st, &g);
+  if (rc != FBF_OK) return rc;
+  if (ticket) *ticket = (fbf_ticket_t)g;
+  return FBF_OK;
+}
+
+int fbf_poll(fbf_batch_t batch, fbf_ticket_t ticket, int* status) {
+  if (!batch || !status) return fbf::set_error(FBF_EINVAL, "fbf_poll: NULL argument");
+  fbf::Batch& b = batch->b;
+  std::lock_guard<std::mutex> lk(b.mu);
+  const int s = fbf::gen_status(&b, (unsigned long long)ticket);
+  if (s != FBF_DONE && s != FBF_PENDING) return s;
+  *status = s;
+  return FBF_OK;
+}
+
+int fbf_wait(fbf_batch_t batch, fbf_ticket_t ticket, double timeout_s) {
+  if (!batch) return fbf::set_error(FBF_EINVAL, "fbf_wait: batch is NULL");
+  if (!(timeout_s >= 0)) return fbf::set_error(FBF_EINVAL, "fbf_wait: timeout must be >= 0");
+  const auto t0 = std::chrono::steady_clock::now();
+  while (true) {
+    int s;
+    {
+      std::lock_guard<std::mutex> lk(batch->b.mu);
+      s = fbf::gen_status(&batch->b, (unsigned long long)ticket);
+    }
+    if (s == FBF_DONE) return FBF_OK;
+    if (s != FBF_PENDING) return s;
+    const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (el >= timeout_s) return fbf::set_error(FBF_ETIMEDOUT, "fbf_wait: timed out");
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+}
+
+int fbf_batch_pending(fbf_batch_t batch, int* n) {
+  if (!batch || !n) return fbf::set_error(FBF_EINVAL, "fbf_batch_pending: NULL argument");
+  std::lock_guard<std::mutex> lk(batch->b.mu);
+  *n = (int)batch->b.pending.size();
+  return FBF_OK;
+}
+
+int fbf_batch_destroy(fbf_batch_t batch) {
+  if (!batch) return FBF_OK;
+  fbf::Batch& b = batch->b;
+  for (auto& g : b.gens) {
+    cudaEventSynchronize(g.ev);
+    cudaEventDestroy(g.ev);
+  }
+  for (auto ev : b.free_events) cudaEventDestroy(ev);
+  if (b.graph) cudaGraphExecDestroy(b.graph);
+  if (b.capture_stream) cudaStreamDestroy(b.capture_stream);
+  for (auto& lb : b.ring) {
+    if (lb.copied) { cudaEventSynchronize(lb.copied); cudaEventDestroy(lb.copied); }
+    if (lb.d) cudaFree(lb.d);
+    if (lb.h) cudaFreeHost(lb.h);
+  }
+  if (b.d_scratch) cudaFree(b.d_scratch);
+  delete batch;
+  return FBF_OK;
+}
+
+}  // extern "C"

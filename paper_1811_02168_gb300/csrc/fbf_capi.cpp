@@ -24,6 +24,10 @@ struct fbf_plan_s {
   Plan p;
 };
 
+namespace fbf {
+const Plan* plan_of(fbf_plan_t h) { return &h->p; }
+}  // namespace fbf
+
 namespace {
 
 int radius_of(double theta) { return (int)std::ceil(3.0 * theta - 1e-12); }

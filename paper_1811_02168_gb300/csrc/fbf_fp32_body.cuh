@@ -1,0 +1,485 @@
+// Shared by the single-image and batched launchers: the FP32 fused Fourier bilateral
+// filter kernel body (see fbf_fp32.cu for the description of the method and schedule).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "fbf_internal.h"
+
+namespace fbf {
+namespace fp32 {
+
+constexpr int TX = 32;                 // tile width
+constexpr int NXH = 8;                 // x outputs per lane in the x pass
+constexpr float kOutside = -3.0e38f;   // marks halo pixels outside the image
+constexpr int TABN = 256;              // per-term (cos, sin) table over integer intensities
+
+template <int RAD, int TY, int NT, int NY>
+struct Cfg {
+  static constexpr int NW = NT / 32;                       // warps
+  static constexpr int HROWS = TY + 2 * RAD;               // rows of the x-pass output
+  static constexpr int HROWS_P = (HROWS + 4 * NW - 1) / (4 * NW) * (4 * NW);  // whole rounds
+  static constexpr int TXH = TX + 2 * RAD;                 // halo tile width
+  static constexpr int FHS = TXH + 1;                      // f-halo row stride (floats)
+  static constexpr int NQ2 = (NXH + 2 * RAD + 1) / 2;      // 16-byte loads per x-pass item
+  static constexpr int SWP0 = 3 * NXH + 2 * NQ2;           // float2 slots read per stage row
+  static constexpr int SWP = SWP0 + ((2 - SWP0 % 16) + 16) % 16;   // == 2 (mod 16)
+  static constexpr int STAGE_F2 = 8 * SWP;                 // per warp: 4 rows x 2 pairs
+  static constexpr int HS2 = TX + 2;                       // x-pass buffer row stride (float2)
+  static constexpr int CPS0 = HROWS_P * HS2;
+  static constexpr int CPS = CPS0 + ((4 - CPS0 % 16) + 16) % 16;  // pair stride, == 4 (mod 16)
+  static constexpr size_t SMEM_BYTES =
+      (size_t)(NW * STAGE_F2 + 2 * CPS + 2 * TABN) * 8 + (size_t)HROWS_P * FHS * 4 + 16;
+  static_assert(TX * TY == NT * NY, "y-pass mapping: one column of NY pixels per thread");
+  static_assert(TY % NY == 0 && (TY / NY) * 32 == NT, "y-pass mapping");
+  static_assert(SMEM_BYTES <= 232448, "shared memory per CTA exceeds 227 KB");
+};
+
+// One image of a launch.  Units of work are (tile, term) pairs of weight 2 (k >= 1) or
+// 1 (k = 0); the images of a launch form one weighted sequence, image after image.
+struct Work {
+  const float* in;
+  float* out;
+  long long pitch;                    // row stride in elements (in and out)
+  int H, W, tiles_x, tiles_y;
+  int K, wtile;                       // wtile = 2K - 1
+  long long tiles;
+  long long wstart;                   // weighted offset of the image's first unit
+  int counter_base;                   // index of the image's first tile counter
+  int param_idx;                      // index of the image's DeviceParams (work-lists)
+};
+
+struct Scratch {
+  long long wtot;                     // total weight of the launch
+  float* partial;                     // G * 2 slots * 2 * NY * NT floats
+  int* counter;                       // one per tile of every image, zero between launches
+};
+
+// A single image whose parameters sit in the constant bank (kernel parameter).
+struct SingleSrc {
+  const DeviceParams* p;
+  Work w;
+  __device__ __forceinline__ int count() const { return 1; }
+  __device__ __forceinline__ Work work(int) const { return w; }
+  __device__ __forceinline__ const DeviceParams& params(int) const { return *p; }
+  __device__ __forceinline__ int find(long long) const { return 0; }
+};
+
+// A device work-list of images (batched launch).
+struct ListSrc {
+  const DeviceParams* __restrict__ prm;
+  const Work* __restrict__ wl;
+  int n;
+  __device__ __forceinline__ int count() const { return n; }
+  __device__ __forceinline__ Work work(int i) const { return wl[i]; }
+  __device__ __forceinline__ const DeviceParams& params(int i) const { return prm[wl[i].param_idx]; }
+  // last image whose weighted start is <= s
+  __device__ __forceinline__ int find(long long s) const {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (wl[mid].wstart <= s) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+  }
+};
+
+__device__ __forceinline__ long long ceil_div_ll(long long a, long long b) { return (a + b - 1) / b; }
+
+// weighted start of term k within a tile (k = 0 weighs 1, k >= 1 weighs 2)
+__device__ __forceinline__ int term_start(int k) { return k == 0 ? 0 : 2 * k - 1; }
+
+// first term of an image whose weighted start is >= s (image-local index tile*K + k)
+__device__ __forceinline__ long long first_term_at(long long s, int K, int wtile) {
+  long long t = s / wtile;
+  long long rem = s - t * wtile;
+  int k = (rem == 0) ? 0 : (int)((rem + 2) / 2);   // smallest k >= 1 with 2k-1 >= rem
+  if (k >= K) { ++t; k = 0; }
+  return t * K + k;
+}
+
+// first unit of the launch whose weighted start is >= s: image i, image-local unit u
+// (i == src.count() past the end)
+template <class Src>
+__device__ __forceinline__ void locate(const Src& src, long long s, long long wtot, int& i,
+                                       long long& u) {
+  if (s >= wtot) { i = src.count(); u = 0; return; }
+  i = src.find(s);
+  const Work w = src.work(i);
+  u = first_term_at(s - w.wstart, w.K, w.wtile);
+  if (u >= w.tiles * w.K) { ++i; u = 0; }
+}
+
+// (cos, sin)(k nu v) for any v: reduce x = k v by the period (n = x - P rint(x/P) lies in
+// [-P/2, P/2]), then the accurate sincospi.  Used for tiles whose values are not all
+// integers in [0, min(R, TABN-1)].
+__device__ __forceinline__ float2 term_cs_any(float kf, float v, const DeviceParams& p) {
+  const float x = kf * v;
+  const float n = fmaf(-rintf(x * p.invP), (float)p.P, x);
+  float s, c;
+  sincospif(n * (2.0f * p.invP), &s, &c);
+  return make_float2(c, s);
+}
+
+// Table of (cos, sin)(k nu v) for integer v = 0..TABN-1: the phase index n = (k v) mod P
+// is exact in integers and exp(i 2 pi n / P) is the product of the plan's two host-rounded
+// tables (n = 128 a + b), so every entry is within a few ulp of the exact value.
+template <int NT>
+__device__ __forceinline__ void build_term_table(const DeviceParams& p, int k, float2* dst2) {
+  float* dst = reinterpret_cast<float*>(dst2);   // [0, TABN): cos, [TABN, 2 TABN): sin
+  for (int v = threadIdx.x; v < TABN; v += NT) {
+    const int n = (k * v) % p.P;
+    const int a = n >> 7, b = n & (kTrigLo - 1);
+    const float ca = p.ta[2 * a], sa = p.ta[2 * a + 1];
+    const float cb = p.tb[2 * b], sb = p.tb[2 * b + 1];
+    dst[v] = fmaf(ca, cb, -sa * sb);
+    dst[TABN + v] = fmaf(sa, cb, ca * sb);
+  }
+}
+
+// table lookup for an integer value 0 <= v < TABN: the index is read from the float's
+// mantissa (v + 2^23 has v in its low bits), which keeps the conversion off the XU pipe
+__device__ __forceinline__ float2 tab_lookup(const float2* tab2, float v) {
+  const float* tab = reinterpret_cast<const float*>(tab2);
+  const unsigned i = __float_as_uint(v + 8388608.0f) & (TABN - 1);
+  return make_float2(tab[i], tab[TABN + i]);
+}
+
+// tap d of 0..2*RAD, read through the symmetric half so only RAD+1 registers are live
+template <int RAD>
+__device__ __forceinline__ float2 tap2(const DeviceParams& p, int d) {
+  const float g = p.g[d <= RAD ? d : 2 * RAD - d];
+  return make_float2(g, g);
+}
+
+// x pass of one item: 8 consecutive outputs of one float2 image pair in one row.
+template <int RAD>
+__device__ __forceinline__ void xconv8(const float2* __restrict__ srow, const DeviceParams& p,
+                                       float2* __restrict__ dst) {
+  constexpr int NQ2 = (NXH + 2 * RAD + 1) / 2;
+  float2 acc[NXH];
+#pragma unroll
+  for (int u = 0; u < NXH; ++u) acc[u] = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int q2 = 0; q2 < NQ2; ++q2) {
+    const float4 v4 = *reinterpret_cast<const float4*>(srow + 2 * q2);
+    const float2 vv[2] = {make_float2(v4.x, v4.y), make_float2(v4.z, v4.w)};
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int q = 2 * q2 + e;
+#pragma unroll
+      for (int u = 0; u < NXH; ++u) {
+        const int d = q - u;
+        if (d >= 0 && d <= 2 * RAD) acc[u] = __ffma2_rn(tap2<RAD>(p, d), vv[e], acc[u]);
+      }
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < NXH; u += 2)
+    *reinterpret_cast<float4*>(dst + u) = make_float4(acc[u].x, acc[u].y, acc[u + 1].x, acc[u + 1].y);
+}
+
+template <int RAD, int TY, int NT, int NY, class Src>
+__device__ __forceinline__ void fbf_body(const Src& src, const Scratch& sc) {
+  using C = Cfg<RAD, TY, NT, NY>;
+  extern __shared__ float4 smem_f4[];
+  float2* smem2 = reinterpret_cast<float2*>(smem_f4);
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const int warp = tid >> 5;
+  float2* stage = smem2 + warp * C::STAGE_F2;
+  float2* hbuf = smem2 + C::NW * C::STAGE_F2;
+  float2* tabs = hbuf + 2 * C::CPS;                    // two term tables (double buffer)
+  float* fh = reinterpret_cast<float*>(tabs + 2 * TABN);
+  __shared__ int s_last;
+
+  const int G = gridDim.x;
+  const int c = blockIdx.x;
+  const long long Lc = ceil_div_ll((long long)c * sc.wtot, G);
+  const long long Lc1 = ceil_div_ll((long long)(c + 1) * sc.wtot, G);
+  int img, img_end, img_first;
+  long long u, u_end, u_first;
+  locate(src, Lc, sc.wtot, img, u);
+  locate(src, Lc1, sc.wtot, img_end, u_end);
+  img_first = img;
+  u_first = u;
+
+  // own pixels: one column of NY rows
+  const int ox = lane;
+  const int oy = warp * NY;
+  // x-pass lane roles (bank-conflict-free 16-byte accesses within each quarter warp)
+  const int x_cp = lane & 1, x_rlo = (lane >> 1) & 1, x_xlo = (lane >> 2) & 1;
+  const int x_rhi = (lane >> 3) & 1, x_xhi = (lane >> 4) & 1;
+  const int x_row4 = x_rhi * 2 + x_rlo;        // 0..3 (k >= 1)
+  const int x_xg = x_xhi * 2 + x_xlo;          // 0..3
+  const int x_row8 = x_row4 * 2 + x_cp;        // 0..7 (k == 0: eight rows, one pair)
+
+  while (img < img_end || (img == img_end && u < u_end)) {
+    const Work wk = src.work(img);
+    const DeviceParams& p = src.params(img);
+    const int K = wk.K;
+    const int H = wk.H, W = wk.W;
+    const long long pitch = wk.pitch;
+    const float* __restrict__ in = wk.in;
+    float* __restrict__ out = wk.out;
+    const float m = p.center;
+    const long long t = u / K;
+    const int kb = (int)(u - t * K);
+    const int ke = (img == img_end && t == u_end / K) ? (int)(u_end - t * K) : K;
+    const int tx0 = (int)(t % wk.tiles_x) * TX;
+    const int ty0 = (int)(t / wk.tiles_x) * TY;
+
+    // f of the tile plus halo (rows padded to whole x-pass rounds); kOutside marks
+    // pixels outside the image.  The tile uses the term tables when all its values are
+    // integers in [0, min(R, TABN-1)] (8-bit images), else the sincospi path.
+    const float vmax = (float)min(p.R, TABN - 1);
+    int ok = 1;
+    for (int i = tid; i < C::HROWS_P * C::TXH; i += NT) {
+      const int row = i / C::TXH, xx = i - row * C::TXH;
+      const int gy = ty0 - RAD + row, gx = tx0 - RAD + xx;
+      float v = kOutside;
+      if (row < C::HROWS && gy >= 0 && gy < H && gx >= 0 && gx < W) {
+        v = __ldg(in + (long)gy * pitch + gx);
+        ok &= (v == rintf(v)) & (v >= 0.f) & (v <= vmax);
+      }
+      fh[row * C::FHS + xx] = v;
+    }
+    // every halo pixel inside the image: generation needs no masking
+    const bool interior = tx0 - RAD >= 0 && ty0 - RAD >= 0 && tx0 + TX + RAD <= W &&
+                          ty0 + TY + RAD <= H;
+    const bool tile_int = __syncthreads_and(ok) != 0;
+    if (tile_int && kb >= 1) {
+      build_term_table<NT>(p, kb, tabs + (kb & 1) * TABN);
+      __syncthreads();
+    }
+
+    float2 num2[NY], den2[NY];
+#pragma unroll
+    for (int a = 0; a < NY; ++a) {
+      num2[a] = make_float2(0.f, 0.f);
+      den2[a] = make_float2(0.f, 0.f);
+    }
+
+    for (int k = kb; k < ke; ++k) {
+      const float kf = (float)k;
+      if (k == 0) {
+        // ---- term 0: pair (f - m, 1); eight halo rows per warp iteration -------------
+        for (int rb = warp * 8; rb < C::HROWS_P; rb += C::NW * 8) {
+#pragma unroll
+          for (int r8 = 0; r8 < 8; ++r8) {
+#pragma unroll
+            for (int xx = lane; xx < C::TXH; xx += 32) {
+              const float v = fh[(rb + r8) * C::FHS + xx];
+              stage[r8 * C::SWP + xx] = (v > kOutside) ? make_float2(v - m, 1.f) : make_float2(0.f, 0.f);
+            }
+          }
+          __syncwarp();
+          xconv8<RAD>(stage + x_row8 * C::SWP + x_xg * NXH, p,
+                      hbuf + (rb + x_row8) * C::HS2 + x_xg * NXH);
+          __syncwarp();
+        }
+      } else {
+        // ---- term k >= 1: pairs (C, S) and (f'C, f'S); four halo rows per iteration --
+        const float2* tab = tabs + (k & 1) * TABN;
+        for (int rb = warp * 4; rb < C::HROWS_P; rb += C::NW * 4) {
+          if (tile_int && interior) {
+#pragma unroll
+            for (int r4 = 0; r4 < 4; ++r4) {
+#pragma unroll
+              for (int xx = lane; xx < C::TXH; xx += 32) {
+                const float v = fh[(rb + r4) * C::FHS + xx];
+                const float2 cs = tab_lookup(tab, v);
+                const float fm = v - m;
+                stage[(r4 * 2) * C::SWP + xx] = cs;
+                stage[(r4 * 2 + 1) * C::SWP + xx] = make_float2(fm * cs.x, fm * cs.y);
+              }
+            }
+          } else if (tile_int) {
+#pragma unroll
+            for (int r4 = 0; r4 < 4; ++r4) {
+#pragma unroll
+              for (int xx = lane; xx < C::TXH; xx += 32) {
+                const float v = fh[(rb + r4) * C::FHS + xx];
+                const bool in_img = v > kOutside;
+                float2 cs = tab_lookup(tab, in_img ? v : 0.f);
+                cs.x = in_img ? cs.x : 0.f;
+                cs.y = in_img ? cs.y : 0.f;
+                const float fm = in_img ? v - m : 0.f;
+                stage[(r4 * 2) * C::SWP + xx] = cs;
+                stage[(r4 * 2 + 1) * C::SWP + xx] = make_float2(fm * cs.x, fm * cs.y);
+              }
+            }
+          } else {
+#pragma unroll
+            for (int r4 = 0; r4 < 4; ++r4) {
+#pragma unroll
+              for (int xx = lane; xx < C::TXH; xx += 32) {
+                const float v = fh[(rb + r4) * C::FHS + xx];
+                const bool in_img = v > kOutside;
+                float2 cs = term_cs_any(kf, in_img ? v : 0.f, p);
+                cs.x = in_img ? cs.x : 0.f;
+                cs.y = in_img ? cs.y : 0.f;
+                const float fm = in_img ? v - m : 0.f;
+                stage[(r4 * 2) * C::SWP + xx] = cs;
+                stage[(r4 * 2 + 1) * C::SWP + xx] = make_float2(fm * cs.x, fm * cs.y);
+              }
+            }
+          }
+          __syncwarp();
+          xconv8<RAD>(stage + (x_row4 * 2 + x_cp) * C::SWP + x_xg * NXH, p,
+                      hbuf + x_cp * C::CPS + (rb + x_row4) * C::HS2 + x_xg * NXH);
+          __syncwarp();
+        }
+      }
+      __syncthreads();
+      // the next term's table goes to the other buffer while this term's is still read
+      if (tile_int && k + 1 < ke) build_term_table<NT>(p, k + 1, tabs + ((k + 1) & 1) * TABN);
+
+      // ---- y pass for own pixels, folded into num/den ---------------------------------
+      const int ncp = (k == 0) ? 1 : 2;
+      float2 w[NY];
+      if (k != 0) {
+        const float ck = p.c[k];
+        const float2* tab = tabs + (k & 1) * TABN;
+#pragma unroll
+        for (int a = 0; a < NY; ++a) {
+          const float v = fh[(oy + a + RAD) * C::FHS + ox + RAD];
+          const bool in_img = v > kOutside;   // false only for pixels past the image edge
+          const float2 cs = tile_int ? tab_lookup(tab, in_img ? v : 0.f) : term_cs_any(kf, v, p);
+          w[a] = make_float2(ck * cs.x, ck * cs.y);
+        }
+      }
+      for (int cp = 0; cp < ncp; ++cp) {
+        float2 acc[NY];
+#pragma unroll
+        for (int a = 0; a < NY; ++a) acc[a] = make_float2(0.f, 0.f);
+        const float2* hcol = hbuf + cp * C::CPS + oy * C::HS2 + ox;
+#pragma unroll
+        for (int q = 0; q < NY + 2 * RAD; ++q) {
+          const float2 v = hcol[q * C::HS2];
+#pragma unroll
+          for (int a = 0; a < NY; ++a) {
+            const int d = q - a;
+            if (d >= 0 && d <= 2 * RAD) acc[a] = __ffma2_rn(tap2<RAD>(p, d), v, acc[a]);
+          }
+        }
+        if (k == 0) {
+          const float c0 = p.c[0];
+#pragma unroll
+          for (int a = 0; a < NY; ++a) {
+            num2[a].x = fmaf(c0, acc[a].x, num2[a].x);   // c_0 B(f - m)
+            den2[a].x = fmaf(c0, acc[a].y, den2[a].x);   // c_0 B(1)
+          }
+        } else if (cp == 0) {
+#pragma unroll
+          for (int a = 0; a < NY; ++a) den2[a] = __ffma2_rn(w[a], acc[a], den2[a]);
+        } else {
+#pragma unroll
+          for (int a = 0; a < NY; ++a) num2[a] = __ffma2_rn(w[a], acc[a], num2[a]);
+        }
+      }
+      __syncthreads();   // hbuf and stage are rewritten by the next term
+    }
+
+    float num[NY], den[NY];
+#pragma unroll
+    for (int a = 0; a < NY; ++a) {
+      num[a] = num2[a].x + num2[a].y;
+      den[a] = den2[a].x + den2[a].y;
+    }
+
+    // ---- finish the tile --------------------------------------------------------------
+    bool finish = true;
+    if (!(kb == 0 && ke == K)) {
+      const int wmine = term_start(ke) - term_start(kb);
+      const int slot = (img_first == img && u_first / K == t) ? 0 : 1;
+      float* pp = sc.partial + ((long long)(c * 2 + slot) * 2) * NY * NT;
+#pragma unroll
+      for (int a = 0; a < NY; ++a) {
+        pp[a * NT + tid] = num[a];
+        pp[(NY + a) * NT + tid] = den[a];
+      }
+      __threadfence();
+      __syncthreads();
+      if (tid == 0) {
+        const int prev = atomicAdd(sc.counter + wk.counter_base + t, wmine);
+        s_last = (prev + wmine == wk.wtile);
+      }
+      __syncthreads();
+      finish = s_last != 0;
+      if (finish) {
+        __threadfence();
+        // sum the partials of all contributing CTAs in CTA (= term) order
+        const long long g0 = wk.wstart + t * wk.wtile;
+        const long long c0 = g0 * G / sc.wtot;
+        const long long c1 = (g0 + term_start(K - 1)) * G / sc.wtot;
+#pragma unroll
+        for (int a = 0; a < NY; ++a) { num[a] = 0.f; den[a] = 0.f; }
+        for (long long cc = c0; cc <= c1; ++cc) {
+          int fi, gi;
+          long long fu, gu;
+          locate(src, ceil_div_ll(cc * sc.wtot, G), sc.wtot, fi, fu);
+          locate(src, ceil_div_ll((cc + 1) * sc.wtot, G), sc.wtot, gi, gu);
+          if (!(fi < gi || (fi == gi && fu < gu))) continue;  // no unit starts in this CTA's range
+          const int sl = (fi == img && fu / K == t) ? 0 : 1;
+          const float* qp = sc.partial + ((cc * 2 + sl) * 2) * NY * NT;
+#pragma unroll
+          for (int a = 0; a < NY; ++a) {
+            num[a] += __ldcg(qp + a * NT + tid);
+            den[a] += __ldcg(qp + (NY + a) * NT + tid);
+          }
+        }
+        if (tid == 0) sc.counter[wk.counter_base + t] = 0;
+      }
+    }
+    if (finish) {
+#pragma unroll
+      for (int a = 0; a < NY; ++a) {
+        const int gy = ty0 + oy + a, gx = tx0 + ox;
+        if (gy < H && gx < W) {
+          const float d = den[a];
+          const float f = fh[(oy + a + RAD) * C::FHS + ox + RAD];
+          out[(long)gy * pitch + gx] = (d > 0.f) ? m + num[a] / d : f;
+        }
+      }
+    }
+    u = t * K + ke;
+    if (u >= wk.tiles * K) { ++img; u = 0; }
+    __syncthreads();   // the f halo is rewritten by the next tile
+  }
+}
+
+// One image, parameters in the constant bank.
+template <int RAD, int TY, int NT, int NY>
+__global__ void __launch_bounds__(NT, 1)
+fbf_fp32_kernel(const __grid_constant__ DeviceParams p, const Work w, const Scratch sc) {
+  const SingleSrc src{&p, w};
+  fbf_body<RAD, TY, NT, NY>(src, sc);
+}
+
+// A device work-list of images sharing one radius class (batched launch).
+template <int RAD, int TY, int NT, int NY>
+__global__ void __launch_bounds__(NT, 1)
+fbf_fp32_batch_kernel(const DeviceParams* __restrict__ params, const Work* __restrict__ work,
+                      int n, const Scratch sc) {
+  const ListSrc src{params, work, n};
+  fbf_body<RAD, TY, NT, NY>(src, sc);
+}
+
+
+// padded copy of a plan's parameters for the RAD instantiation (taps beyond the plan's
+// radius are zero, so a wider instantiation serves a smaller r)
+template <int RAD>
+inline DeviceParams pad_params(const DeviceParams& dp) {
+  DeviceParams p = dp;
+  float g[2 * FBF_MAX_RADIUS + 1];
+  for (int i = 0; i <= 2 * RAD; ++i) {
+    const int d = i - (RAD - dp.r);
+    g[i] = (d >= 0 && d <= 2 * dp.r) ? dp.g[d] : 0.f;
+  }
+  for (int i = 0; i <= 2 * RAD; ++i) p.g[i] = g[i];
+  p.r = RAD;
+  return p;
+}
+
+}  // namespace fp32
+}  // namespace fbf

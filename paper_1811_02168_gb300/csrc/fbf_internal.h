@@ -8,6 +8,9 @@
 
 #include "fbf.h"
 
+struct CUstream_st;
+using cudaStream_t_ = CUstream_st*;
+
 namespace fbf {
 
 // ---- host fitter (fbf_fit.cpp) --------------------------------------------------------
@@ -58,6 +61,9 @@ struct Plan {
   DeviceParams dp{};
 };
 
+// the Plan behind a C handle (defined with the handle type in fbf_capi.cpp)
+const Plan* plan_of(fbf_plan_t h);
+
 // ---- errors ---------------------------------------------------------------------------
 int set_error(int code, const std::string& msg);
 void clear_error();
@@ -66,6 +72,10 @@ void clear_error();
 // FP32 fused kernel launcher (fbf_fp32.cu).
 int launch_fp32(const DeviceParams& dp, const float* in, float* out, int H, int W,
                 size_t pitch, void* stream);
+// Per-(device, stream) scratch: `counters` zeroed ints (left at zero by every launch) and
+// `partial_bytes` of partial sums; grown with cudaMalloc when too small.
+int get_workspace(int dev, cudaStream_t_ st, size_t partial_bytes, size_t counters,
+                  float** partial, int** counter);
 // Same kernel, scratch from a fixed device array instead of the per-stream workspace.
 int launch_fp32_noalloc(const DeviceParams& dp, const float* in, float* out, int H, int W,
                         size_t pitch, void* stream);

@@ -165,3 +165,33 @@ def test_plan_info_null_plan():
     with pytest.raises(B.FbfError) as ei:
         B.fbf_plan_info(0)
     assert ei.value.code == B.FBF_EINVAL
+
+
+def test_batch_host_side_queue_and_bounded_wait():
+    """Batch bookkeeping needs no GPU until a launch: queueing, the max_images bound
+    (FBF_EBUSY), argument checks, and a bounded wait on a launch that never happens."""
+    p = B.Plan(30.0, 255, 3.0, K=4)
+    b = B.fbf_batch_create(2, 0)
+    try:
+        t0 = B.fbf_submit(b, p.handle, 1 << 20, 1 << 30, 16, 16, 16)
+        t1 = B.fbf_submit(b, p.handle, 1 << 21, 1 << 31, 8, 9, 9)
+        assert t0 == t1                       # same pending launch
+        assert B.fbf_batch_pending(b) == 2
+        with pytest.raises(B.FbfError) as ei:
+            B.fbf_submit(b, p.handle, 1 << 22, 1 << 32, 4, 4, 4)
+        assert ei.value.code == B.FBF_EBUSY
+        for kw in (dict(d_in=0), dict(H=0), dict(pitch_elems=2)):
+            args = dict(d_in=1 << 23, d_out=1 << 33, H=4, W=4, pitch_elems=4)
+            args.update(kw)
+            with pytest.raises(B.FbfError) as ei:
+                B.fbf_submit(b, p.handle, args["d_in"], args["d_out"], args["H"], args["W"],
+                             args["pitch_elems"])
+            assert ei.value.code in (B.FBF_EINVAL, B.FBF_EBUSY)
+        assert B.fbf_poll(b, t0) == B.FBF_PENDING
+        with pytest.raises(B.FbfError) as ei:
+            B.fbf_wait(b, t0, 0.05)
+        assert ei.value.code == B.FBF_ETIMEDOUT
+    finally:
+        B.fbf_batch_destroy(b)
+    with pytest.raises(B.FbfError):
+        B.fbf_batch_create(0, 0)

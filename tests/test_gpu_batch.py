@@ -1,0 +1,131 @@
+"""Batched form (one persistent launch over many images, CUDA graph capture/replay) on
+the GPU, through the C ABI.  Every image must match its one-at-a-time fbf_filter result
+within the FP32 tolerance, and the oracle where the oracle is cheap."""
+import numpy as np
+import pytest
+
+from oracle import fit as ofit
+from oracle import filters as ofl
+from paper_1811_02168_gb300.synth import voronoi_image
+
+pytestmark = pytest.mark.gpu
+TOL = 5e-3
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def B():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1811_02168_gb300 import build
+    build.build()
+    from paper_1811_02168_gb300 import binding
+    binding.lib()
+    return binding
+
+
+def _mixed_jobs(n, seed):
+    rng = np.random.default_rng(seed)
+    jobs = []
+    for i in range(n):
+        H = int(rng.integers(40, 400))
+        W = int(rng.integers(40, 400))
+        theta = float(rng.choice([1.0, 2.0, 5.0, 10.0]))
+        sigma = float(rng.choice([10.0, 30.0, 80.0]))
+        K = int(rng.choice([3, 5, 8]))
+        jobs.append((H, W, theta, sigma, K, seed * 100 + i))
+    return jobs
+
+
+def _single(B, plan, x):
+    y = torch.empty_like(x)
+    H, W = x.shape
+    B.fbf_filter(plan.handle, x.data_ptr(), y.data_ptr(), H, W, W, torch.cuda.current_stream().cuda_stream)
+    return y
+
+
+@pytest.mark.parametrize("autotune", [False, True])
+def test_batch_matches_single_launches_alone_vs_in_mix(B, autotune):
+    """Each image filtered in the mix (one launch per radius class over all images) equals
+    the same image filtered alone, within the FP32 tolerance."""
+    jobs = _mixed_jobs(14, 3 + autotune)
+    plans = {}
+    xs, ys, refs = [], [], []
+    batch = B.Batch(32, autotune=autotune)
+    for H, W, theta, sigma, K, seed in jobs:
+        key = (theta, sigma, K)
+        if key not in plans:
+            plans[key] = B.Plan(sigma, 255, theta, K=K)
+        x = torch.from_numpy(voronoi_image(H, W, 8, 30.0, 10.0, seed=seed)).cuda()
+        y = torch.full_like(x, -5.0)
+        xs.append(x)
+        ys.append(y)
+        refs.append(_single(B, plans[key], x))
+        batch.submit(plans[key], x, y)
+    batch.launch()
+    torch.cuda.synchronize()
+    for y, ref in zip(ys, refs):
+        assert float((y - ref).abs().max()) <= TOL
+    batch.close()
+
+
+def test_batch_against_oracle(B):
+    jobs = [(70, 90, 2.0, 30.0, 5, 1), (33, 150, 5.0, 10.0, 8, 2), (120, 64, 2.0, 80.0, 3, 3)]
+    batch = B.Batch(8)
+    outs = []
+    for H, W, theta, sigma, K, seed in jobs:
+        img = voronoi_image(H, W, 8, 30.0, 10.0, seed=seed)
+        plan = B.Plan(sigma, 255, theta, K=K)
+        x = torch.from_numpy(img).cuda()
+        y = torch.empty_like(x)
+        t = batch.submit(plan, x, y)
+        outs.append((img, plan, x, y, theta, sigma, K))
+    batch.launch()
+    batch.wait(t, 60.0)
+    assert batch.poll(t) == B.FBF_DONE
+    for img, plan, x, y, theta, sigma, K in outs:
+        op = ofit.make_plan(sigma, 255, K=K)
+        ref = ofl.fourier_bf(img.astype(np.float64), theta, op.c, op.T)
+        assert np.abs(y.cpu().numpy() - ref).max() <= TOL
+    batch.close()
+
+
+def test_graph_capture_and_replay_follow_new_input(B):
+    """Capture once, replay twice with new contents in the same input buffers: each replay
+    equals fbf_filter on the contents of that moment."""
+    jobs = _mixed_jobs(6, 9)
+    batch = B.Batch(8)
+    items = []
+    for H, W, theta, sigma, K, seed in jobs:
+        plan = B.Plan(sigma, 255, theta, K=K)
+        x = torch.from_numpy(voronoi_image(H, W, 8, 30.0, 10.0, seed=seed)).cuda()
+        y = torch.empty_like(x)
+        batch.submit(plan, x, y)
+        items.append((plan, x, y, H, W))
+    batch.capture()
+    assert batch.pending() == 0
+    for rep in range(2):
+        for i, (plan, x, y, H, W) in enumerate(items):
+            x.copy_(torch.from_numpy(voronoi_image(H, W, 8, 30.0, 10.0, seed=1000 * rep + i)).cuda())
+        t = batch.replay()
+        batch.wait(t, 60.0)
+        for plan, x, y, H, W in items:
+            assert float((y - _single(B, plan, x)).abs().max()) <= TOL
+    batch.close()
+
+
+def test_launches_in_a_row_reuse_the_work_list_ring(B):
+    """More launches than work-list slots, without synchronising in between."""
+    plan = B.Plan(30.0, 255, 2.0, K=4)
+    batch = B.Batch(4)
+    xs = [torch.from_numpy(voronoi_image(64 + 8 * i, 80, 6, 30.0, 10.0, seed=i)).cuda() for i in range(9)]
+    ys = [torch.empty_like(x) for x in xs]
+    tickets = []
+    for x, y in zip(xs, ys):
+        tickets.append(batch.submit(plan, x, y))
+        batch.launch()
+    batch.wait(tickets[-1], 60.0)
+    assert all(batch.poll(t) == B.FBF_DONE for t in tickets)
+    for x, y in zip(xs, ys):
+        assert float((y - _single(B, plan, x)).abs().max()) <= TOL
+    batch.close()
