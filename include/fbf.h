@@ -167,7 +167,8 @@ int fbf_batch_create(fbf_batch_t* out, int max_images, int flags);
 
 /*
  * fbf_submit -- queue one image (host-side only; nothing runs until fbf_launch).  Arguments
- * as fbf_filter; FBF_FP32 plans only.  The plan must outlive the launch that uses it.
+ * as fbf_filter; FBF_FP32 plans only.  The plan must stay alive until the fbf_launch or
+ * fbf_batch_capture call that takes the image returns (its parameters are copied then).
  * *ticket (may be NULL) identifies the launch the image will belong to.
  * Errors: FBF_EINVAL (bad arguments), FBF_EBUSY (max_images already queued),
  * FBF_EUNSUPPORTED (other precision forms, radius beyond FBF_MAX_RADIUS).

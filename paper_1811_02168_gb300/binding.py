@@ -290,11 +290,13 @@ class Batch:
         import torch
         st = stream if stream is not None else torch.cuda.current_stream()
         fbf_launch(self.handle, st.cuda_stream)
+        self._keep.clear()       # the launch copied the plans' parameters
 
     def capture(self, stream=None):
         import torch
         st = stream if stream is not None else torch.cuda.current_stream()
         fbf_batch_capture(self.handle, st.cuda_stream)
+        self._keep.clear()
 
     def replay(self, stream=None) -> int:
         import torch
