@@ -47,6 +47,9 @@ extern "C" {
 
 /* ---- precision forms (fbf_plan's `precision`) --------------------------------- */
 #define FBF_FP32       0   /* FP32 channel stack and FP32 FIR on the CUDA cores       */
+#define FBF_FP16_TC    1   /* FP16 channel stack, both Gaussian passes on the tensor
+                              cores (tcgen05, banded Toeplitz operand), FP32 accumulate */
+#define FBF_BF16_TC    2   /* as FBF_FP16_TC with BF16 operands                      */
 
 /* ---- flags (fbf_plan's `flags`) ----------------------------------------------- */
 #define FBF_FLAG_FIXED_PERIOD 1  /* T = R (fixed period, the FBF model the paper
@@ -56,6 +59,7 @@ extern "C" {
 #define FBF_MAX_K       64  /* cosine terms                                       */
 #define FBF_MAX_RADIUS  48  /* spatial radius r = ceil(3 theta)                   */
 #define FBF_MAX_PERIOD  65535 /* 2T+1                                             */
+#define FBF_MAX_RADIUS_TC 30  /* radius limit of the tensor-core forms            */
 
 typedef struct fbf_plan_s* fbf_plan_t;
 
@@ -206,6 +210,12 @@ int fbf_batch_destroy(fbf_batch_t batch);
 
 /* fbf_last_error -- message for the last failing call on this thread ("" if none). */
 const char* fbf_last_error(void);
+
+/* fbf_device_errors -- synchronise nothing; read (and with clear != 0 reset) the device
+ * error word of the tensor-core kernels: bit 0 set means a bounded wait inside a kernel
+ * gave up and that launch's output is incomplete.  Read it after synchronising the
+ * stream of the launches in question. */
+int fbf_device_errors(int* flags, int clear);
 
 /* fbf_version -- library version string. */
 const char* fbf_version(void);

@@ -18,6 +18,8 @@ LIB_PATH = os.path.join(HERE, "libfbf.so")
 FBF_OK, FBF_EINVAL, FBF_ENOMEM, FBF_ECUDA, FBF_ETIMEDOUT, FBF_EBUSY = 0, 1, 2, 3, 4, 5
 FBF_PENDING, FBF_DONE, FBF_EUNSUPPORTED = 6, 7, 8
 FBF_FP32 = 0
+FBF_FP16_TC = 1
+FBF_BF16_TC = 2
 FBF_FLAG_FIXED_PERIOD = 1
 FBF_MAX_K = 64
 FBF_MAX_RADIUS = 48
@@ -64,6 +66,7 @@ SIGNATURES = {
     "fbf_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_double]),
     "fbf_batch_pending": (ctypes.c_int, [ctypes.c_void_p, _c_int_p]),
     "fbf_batch_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "fbf_device_errors": (ctypes.c_int, [_c_int_p, ctypes.c_int]),
     "fbf_last_error": (ctypes.c_char_p, []),
     "fbf_version": (ctypes.c_char_p, []),
     "fbf_debug_error_curve": (ctypes.c_int, [_c_double_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -188,6 +191,12 @@ def fbf_batch_pending(batch: int) -> int:
 
 def fbf_batch_destroy(batch: int) -> None:
     _check(lib().fbf_batch_destroy(batch), "fbf_batch_destroy")
+
+
+def fbf_device_errors(clear: bool = False) -> int:
+    f = ctypes.c_int()
+    _check(lib().fbf_device_errors(ctypes.byref(f), 1 if clear else 0), "fbf_device_errors")
+    return f.value
 
 
 def fbf_last_error() -> str:

@@ -33,7 +33,7 @@ namespace {
 int radius_of(double theta) { return (int)std::ceil(3.0 * theta - 1e-12); }
 
 bool precision_known(int precision) {
-  return precision == FBF_FP32;
+  return precision == FBF_FP32 || precision == FBF_FP16_TC || precision == FBF_BF16_TC;
 }
 
 int build_plan(fbf_plan_t* out, const double* b, int R, double theta, int K, double eps,
@@ -50,6 +50,8 @@ int build_plan(fbf_plan_t* out, const double* b, int R, double theta, int K, dou
   const int r = radius_of(theta);
   if (r > FBF_MAX_RADIUS)
     return fbf::set_error(FBF_EUNSUPPORTED, "fbf_plan: radius ceil(3 theta) exceeds FBF_MAX_RADIUS");
+  if (precision != FBF_FP32 && r > FBF_MAX_RADIUS_TC)
+    return fbf::set_error(FBF_EUNSUPPORTED, "fbf_plan: the tensor-core forms support r <= FBF_MAX_RADIUS_TC");
   if (K > FBF_MAX_K) return fbf::set_error(FBF_EUNSUPPORTED, "fbf_plan: K exceeds FBF_MAX_K");
 
   fbf_plan_s* h = new (std::nothrow) fbf_plan_s();
@@ -168,6 +170,9 @@ int fbf_filter(fbf_plan_t plan, const float* d_in, float* d_out, int H, int W,
   switch (plan->p.precision) {
     case FBF_FP32:
       return fbf::launch_fp32(plan->p.dp, d_in, d_out, H, W, pitch_elems, cuda_stream);
+    case FBF_FP16_TC:
+    case FBF_BF16_TC:
+      return fbf::launch_tc(plan->p.dp, d_in, d_out, H, W, pitch_elems, cuda_stream, plan->p.precision);
     default:
       return fbf::set_error(FBF_EINVAL, "fbf_filter: unknown precision form");
   }
@@ -191,6 +196,11 @@ int fbf_filter_noalloc(fbf_plan_t plan, const float* d_in, float* d_out, int H, 
 const char* fbf_last_error(void) { return fbf::g_last_error.c_str(); }
 
 const char* fbf_version(void) { return "fbf-gb300 0.1"; }
+
+int fbf_device_errors(int* flags, int clear) {
+  if (!flags) return fbf::set_error(FBF_EINVAL, "fbf_device_errors: flags is NULL");
+  return fbf::device_errors(flags, clear);
+}
 
 // Test hook: E(K,T) for K = 1..Kc at one T from the C++ fitter (host only).
 int fbf_debug_error_curve(const double* b, int R, int T, int Kc, double* E_out) {

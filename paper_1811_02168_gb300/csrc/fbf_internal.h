@@ -76,6 +76,11 @@ int launch_fp32(const DeviceParams& dp, const float* in, float* out, int H, int 
 // `partial_bytes` of partial sums; grown with cudaMalloc when too small.
 int get_workspace(int dev, cudaStream_t_ st, size_t partial_bytes, size_t counters,
                   float** partial, int** counter);
+// Tensor-core forms (fbf_tc.cu): precision FBF_FP16_TC or FBF_BF16_TC.
+int launch_tc(const DeviceParams& dp, const float* in, float* out, int H, int W, size_t pitch,
+              void* stream, int precision);
+// Device error word of the tensor-core kernels (bit 0: a bounded wait gave up).
+int device_errors(int* flags, int clear);
 // Same kernel, scratch from a fixed device array instead of the per-stream workspace.
 int launch_fp32_noalloc(const DeviceParams& dp, const float* in, float* out, int H, int W,
                         size_t pitch, void* stream);

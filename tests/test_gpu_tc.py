@@ -1,0 +1,76 @@
+"""Tensor-core forms (FBF_FP16_TC, FBF_BF16_TC) against the FP64 oracle, through the C ABI.
+
+Both Gaussian passes run on the tensor cores with FP16 or BF16 operands (the convolved
+images, the banded Toeplitz tap matrix and the x-pass result are rounded to the operand
+type) and FP32 accumulation.  Tolerances: the FP16 form must meet the 0.5 gray-level bound
+stated for the low-precision stack; measured maxima are ~0.13.  The BF16 form
+(7-bit mantissa) measures up to ~0.8 at sigma = 10 and is checked against 1.5 only, to catch
+gross errors; it does not meet the 0.5 bound.
+"""
+import numpy as np
+import pytest
+
+from oracle import fit as ofit
+from oracle import filters as ofl
+from paper_1811_02168_gb300.synth import voronoi_image
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+TOL = {"fp16": 0.5, "bf16": 1.5}
+
+
+@pytest.fixture(scope="module")
+def B():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1811_02168_gb300 import build
+    build.build()
+    from paper_1811_02168_gb300 import binding
+    binding.lib()
+    binding.fbf_device_errors(clear=True)
+    return binding
+
+
+def _run(B, plan, img):
+    x = torch.from_numpy(np.ascontiguousarray(img, np.float32)).cuda()
+    y = torch.full_like(x, -9.0)
+    H, W = img.shape
+    B.fbf_filter(plan.handle, x.data_ptr(), y.data_ptr(), H, W, W, torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    return y.cpu().numpy()
+
+
+CASES = [((256, 256), 3.0, 30.0, 4), ((300, 419), 5.0, 10.0, 12), ((140, 200), 10.0, 10.0, 16),
+         ((129, 257), 2.0, 80.0, 4), ((1, 1), 2.0, 30.0, 4), ((7, 300), 5.0, 30.0, 6),
+         ((260, 33), 10.0, 80.0, 8)]
+
+
+@pytest.mark.parametrize("form", ["fp16", "bf16"])
+@pytest.mark.parametrize("shape,theta,sigma,K", CASES)
+def test_tc_form_against_oracle(B, form, shape, theta, sigma, K):
+    img = voronoi_image(shape[0], shape[1], 12, 40.0, 10.0, seed=shape[0] * 7 + shape[1])
+    prec = B.FBF_FP16_TC if form == "fp16" else B.FBF_BF16_TC
+    plan = B.Plan(sigma, 255, theta, K=K, precision=prec)
+    op = ofit.make_plan(sigma, 255, K=K)
+    ref = ofl.fourier_bf(img.astype(np.float64), theta, op.c, op.T)
+    out = _run(B, plan, img)
+    err = float(np.abs(out - ref).max())
+    assert err <= TOL[form], err
+    assert B.fbf_device_errors() == 0
+
+
+def test_tc_non_integer_input(B):
+    rng = np.random.default_rng(5)
+    img = (voronoi_image(150, 170, 12, 30.0, 10.0, seed=31) * 0.9 +
+           rng.uniform(0.0, 0.999, (150, 170))).astype(np.float32)
+    plan = B.Plan(20.0, 255, 3.0, K=8, precision=B.FBF_FP16_TC)
+    op = ofit.make_plan(20.0, 255, K=8)
+    ref = ofl.fourier_bf(img.astype(np.float64), 3.0, op.c, op.T)
+    assert float(np.abs(_run(B, plan, img) - ref).max()) <= TOL["fp16"]
+    assert B.fbf_device_errors() == 0
+
+
+def test_tc_radius_limit(B):
+    with pytest.raises(B.FbfError) as ei:
+        B.Plan(30.0, 255, 10.5, K=4, precision=B.FBF_FP16_TC)   # r = 32 > 30
+    assert ei.value.code == B.FBF_EUNSUPPORTED
