@@ -51,8 +51,8 @@ struct TcCfg {
   static constexpr int NH = KP;                           // x-pass N (halo rows, padded)
   static constexpr int OPB = TT * KP * 2;                 // bytes of G or B_v
   static constexpr int BHB = NH * KP * 2;                 // bytes of one B_h
-  static constexpr int FHS = (HW + 7) / 8 * 8;            // f-halo row stride (bytes)
-  static constexpr int FHB = ((HW * FHS) + 127) / 128 * 128;
+  static constexpr int FHS = KP + 8;                      // f-halo row stride (bytes), == 8 (mod 16)
+  static constexpr int FHB = ((NH * FHS) + 127) / 128 * 128;   // rows up to NH (padding is finite)
   static constexpr int TABB = 3 * 4 * 256 * 4;            // 3 term-table slots (cos, sin, (f-m)cos, (f-m)sin)
   static constexpr int FIXED = 2 * OPB + FHB + TABB + 128;
   static constexpr int NBH = (FIXED + 2 * BHB + 1024 <= 232448) ? 2 : 1;
@@ -182,7 +182,10 @@ __device__ __forceinline__ void build_tables(const DeviceParams& p, int k, float
 }
 
 // Generate image `KIND` of term k over the halo tile into a K-major operand (rows = halo
-// rows, K = halo columns; rows and columns past the halo are zero).
+// rows, K = halo columns).  Eight consecutive threads fill the eight rows of one core matrix,
+// so the 16-byte stores are conflict-free.  Rows and columns past the halo need only be
+// finite: the matching entries of G are zero.  Pixels outside the image are zero (only
+// tiles at the image border test for them, with a column bit mask per 8-pixel group).
 template <int RAD, typename T, int KIND>
 __device__ __forceinline__ void generate(unsigned char* dst, const unsigned char* fh, const float* tab,
                                          bool tile_int, bool interior, int tx0, int ty0, int H, int W,
@@ -190,14 +193,22 @@ __device__ __forceinline__ void generate(unsigned char* dst, const unsigned char
                                          const DeviceParams& p) {
   using C = TcCfg<RAD>;
   constexpr int KP = C::KP;
+  constexpr int KG = KP / 8;
   const float m = p.center;
-  for (int i = threadIdx.x; i < C::NH * (KP / 8); i += NTHREADS) {
-    const int hy = i / (KP / 8), hx0 = (i - hy * (KP / 8)) * 8;
+  const int col_lo = max(0, RAD - tx0), col_hi = min(C::HW, W - tx0 + RAD);   // inside: [lo, hi)
+  for (int i = threadIdx.x; i < C::NH * KG; i += NTHREADS) {
+    const int hy = ((i >> 3) / KG) * 8 + (i & 7);
+    const int hx0 = ((i >> 3) % KG) * 8;
     float v8[8];
     if (tile_int) {
-      uint2 bytes = make_uint2(0, 0);
-      if (hy < C::HW) bytes = *reinterpret_cast<const uint2*>(fh + hy * C::FHS + hx0);
-      const bool fast = interior && hy < C::HW && hx0 + 8 <= C::HW;
+      const uint2 bytes = *reinterpret_cast<const uint2*>(fh + hy * C::FHS + hx0);
+      unsigned mask = 0xFFu;
+      if (!interior) {
+        const int gy = ty0 - RAD + hy;
+        const bool row_in = hy < C::HW && gy >= 0 && gy < H;
+        const int a = min(8, max(0, col_lo - hx0)), b = min(8, max(0, col_hi - hx0));
+        mask = row_in && b > a ? (((1u << b) - 1u) & ~((1u << a) - 1u)) : 0u;
+      }
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
         const unsigned bv = ((j < 4 ? bytes.x : bytes.y) >> (8 * (j & 3))) & 0xFFu;
@@ -205,12 +216,7 @@ __device__ __forceinline__ void generate(unsigned char* dst, const unsigned char
         if (KIND == CH_FM) val = (float)bv - m;
         else if (KIND == CH_ONE) val = 1.f;
         else val = tab[(KIND == CH_C ? 0 : KIND == CH_S ? 256 : KIND == CH_FC ? 512 : 768) + bv];
-        if (!fast) {
-          const int hx = hx0 + j, gy = ty0 - RAD + hy, gx = tx0 - RAD + hx;
-          const bool inside = hy < C::HW && hx < C::HW && gy >= 0 && gy < H && gx >= 0 && gx < W;
-          val = inside ? val : 0.f;
-        }
-        v8[j] = val;
+        v8[j] = ((mask >> j) & 1u) ? val : 0.f;
       }
     } else {
 #pragma unroll
@@ -347,11 +353,11 @@ fbf_tc_kernel(const __grid_constant__ DeviceParams p, const Work w, const Scratc
     // image is an integer in [0, min(R, 255)], else values are read from global memory
     const float vmax = (float)min(p.R, 255);
     int ok = 1;
-    for (int i = tid; i < C::HW * C::HW; i += NTHREADS) {
-      const int hy = i / C::HW, hx = i - hy * C::HW;
+    for (int i = tid; i < C::NH * C::FHS; i += NTHREADS) {
+      const int hy = i / C::FHS, hx = i - hy * C::FHS;
       const int gy = ty0 - RAD + hy, gx = tx0 - RAD + hx;
       unsigned char b = 0;
-      if (gy >= 0 && gy < H && gx >= 0 && gx < W) {
+      if (hy < C::HW && hx < C::HW && gy >= 0 && gy < H && gx >= 0 && gx < W) {
         const float v = __ldg(w.in + (long long)gy * pitch + gx);
         ok &= (v == rintf(v)) & (v >= 0.f) & (v <= vmax);
         b = (unsigned char)(int)fminf(fmaxf(v, 0.f), 255.f);
@@ -369,6 +375,7 @@ fbf_tc_kernel(const __grid_constant__ DeviceParams p, const Work w, const Scratc
     }
     const bool tile_int = __syncthreads_and(ok) != 0;
 
+    const unsigned char* own = sFh + (oy + RAD) * C::FHS + ox0 + RAD;   // own pixels' intensities
     float nm[32], dn[32];   // num / den of the thread's 32 pixels
 #pragma unroll
     for (int i = 0; i < 32; ++i) { nm[i] = 0.f; dn[i] = 0.f; }
@@ -406,42 +413,53 @@ fbf_tc_kernel(const __grid_constant__ DeviceParams p, const Work w, const Scratc
         const bool to_num = (kindp == CH_FM || kindp == CH_FC || kindp == CH_FS);
         const int woff = (kindp == CH_S || kindp == CH_FS) ? 256 : 0;
 #pragma unroll
-        for (int h = 0; h < 4; ++h) {
-          uint32_t a[8];
-          tmem_ld8(tD2 + ((uint32_t)(32 * q) << 16) + (uint32_t)(ox0 + 8 * h), a);
+        for (int h = 0; h < 2; ++h) {
+          uint32_t a[16];
+          tmem_ld16(tD2 + ((uint32_t)(32 * q) << 16) + (uint32_t)(ox0 + 16 * h), a);
           tmem_wait_ld();
 #pragma unroll
-          for (int i = 0; i < 8; ++i) {
+          for (int ii = 0; ii < 16; ++ii) {
+            const int i = 16 * h + ii;
             float wgt = ck;
             if (kindp >= CH_C) {
-              const int x = ox0 + 8 * h + i;
               if (tile_int) {
-                wgt = ck * tab[woff + sFh[(oy + RAD) * C::FHS + x + RAD]];
+                wgt = ck * tab[woff + own[i]];
               } else {
-                const int gy = ty0 + oy, gx = tx0 + x;
+                const int gy = ty0 + oy, gx = tx0 + ox0 + i;
                 const float fv = (gy < H && gx < W) ? __ldg(w.in + (long long)gy * pitch + gx) : 0.f;
                 const float2 cs = term_cs_any((float)kp, fv, p);
                 wgt = ck * (woff ? cs.y : cs.x);
               }
             }
-            const float v = __uint_as_float(a[i]);
-            if (to_num) nm[8 * h + i] = fmaf(wgt, v, nm[8 * h + i]);
-            else dn[8 * h + i] = fmaf(wgt, v, dn[8 * h + i]);
+            const float v = __uint_as_float(a[ii]);
+            if (to_num) nm[i] = fmaf(wgt, v, nm[i]);
+            else dn[i] = fmaf(wgt, v, dn[i]);
           }
         }
       }
       // ---- D1 -> B_v (rounded to the operand type) ------------------------------------
       {
         const uint32_t d1 = tmem + 192u * (uint32_t)(c % L) + ((uint32_t)(32 * q) << 16);
-        for (int j = cg; j < C::NH / 8; j += 4) {
-          uint32_t r[8];
-          tmem_ld8(d1 + 8 * j, r);
+        constexpr int NJ = (C::NH / 8 + 3) / 4;   // chunks of 8 columns per warp
+#pragma unroll
+        for (int j0 = 0; j0 < NJ; j0 += 2) {      // two chunks per batch of TMEM loads
+          uint32_t r[2][8];
+#pragma unroll
+          for (int jj = 0; jj < 2; ++jj) {
+            const int j = cg + 4 * (j0 + jj);
+            if (j0 + jj < NJ && j < C::NH / 8) tmem_ld8(d1 + 8 * j, r[jj]);
+          }
           tmem_wait_ld();
-          *reinterpret_cast<uint4*>(sBv + core_off<KP>(32 * q + lane, 8 * j)) =
-              make_uint4(pack2<T>(__uint_as_float(r[0]), __uint_as_float(r[1])),
-                         pack2<T>(__uint_as_float(r[2]), __uint_as_float(r[3])),
-                         pack2<T>(__uint_as_float(r[4]), __uint_as_float(r[5])),
-                         pack2<T>(__uint_as_float(r[6]), __uint_as_float(r[7])));
+#pragma unroll
+          for (int jj = 0; jj < 2; ++jj) {
+            const int j = cg + 4 * (j0 + jj);
+            if (j0 + jj < NJ && j < C::NH / 8)
+              *reinterpret_cast<uint4*>(sBv + core_off<KP>(32 * q + lane, 8 * j)) =
+                  make_uint4(pack2<T>(__uint_as_float(r[jj][0]), __uint_as_float(r[jj][1])),
+                             pack2<T>(__uint_as_float(r[jj][2]), __uint_as_float(r[jj][3])),
+                             pack2<T>(__uint_as_float(r[jj][4]), __uint_as_float(r[jj][5])),
+                             pack2<T>(__uint_as_float(r[jj][6]), __uint_as_float(r[jj][7])));
+          }
         }
       }
       // table for the term of image c + L if it starts one
@@ -491,29 +509,29 @@ fbf_tc_kernel(const __grid_constant__ DeviceParams p, const Work w, const Scratc
       const bool to_num = (kindp == CH_FM || kindp == CH_FC || kindp == CH_FS);
       const int woff = (kindp == CH_S || kindp == CH_FS) ? 256 : 0;
 #pragma unroll
-      for (int h = 0; h < 4; ++h) {
-        uint32_t a[8];
-        tmem_ld8(tD2 + ((uint32_t)(32 * q) << 16) + (uint32_t)(ox0 + 8 * h), a);
-        tmem_wait_ld();
+        for (int h = 0; h < 2; ++h) {
+          uint32_t a[16];
+          tmem_ld16(tD2 + ((uint32_t)(32 * q) << 16) + (uint32_t)(ox0 + 16 * h), a);
+          tmem_wait_ld();
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          float wgt = ck;
-          if (kindp >= CH_C) {
-            const int x = ox0 + 8 * h + i;
-            if (tile_int) {
-              wgt = ck * tab[woff + sFh[(oy + RAD) * C::FHS + x + RAD]];
-            } else {
-              const int gy = ty0 + oy, gx = tx0 + x;
-              const float fv = (gy < H && gx < W) ? __ldg(w.in + (long long)gy * pitch + gx) : 0.f;
-              const float2 cs = term_cs_any((float)kp, fv, p);
-              wgt = ck * (woff ? cs.y : cs.x);
+          for (int ii = 0; ii < 16; ++ii) {
+            const int i = 16 * h + ii;
+            float wgt = ck;
+            if (kindp >= CH_C) {
+              if (tile_int) {
+                wgt = ck * tab[woff + own[i]];
+              } else {
+                const int gy = ty0 + oy, gx = tx0 + ox0 + i;
+                const float fv = (gy < H && gx < W) ? __ldg(w.in + (long long)gy * pitch + gx) : 0.f;
+                const float2 cs = term_cs_any((float)kp, fv, p);
+                wgt = ck * (woff ? cs.y : cs.x);
+              }
             }
+            const float v = __uint_as_float(a[ii]);
+            if (to_num) nm[i] = fmaf(wgt, v, nm[i]);
+            else dn[i] = fmaf(wgt, v, dn[i]);
           }
-          const float v = __uint_as_float(a[i]);
-          if (to_num) nm[8 * h + i] = fmaf(wgt, v, nm[8 * h + i]);
-          else dn[8 * h + i] = fmaf(wgt, v, dn[8 * h + i]);
         }
-      }
     }
     tc_fence_before();
 
