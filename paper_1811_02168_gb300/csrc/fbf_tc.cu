@@ -68,19 +68,37 @@ struct TcCfg {
   static constexpr int KX = (HX + 15) / 16 * 16;          // x-pass K
   static constexpr int HY = TILE_Y + 2 * RAD;             // halo rows
   static constexpr int KY = (HY + 15) / 16 * 16;          // x-pass N = y-pass K
-  static constexpr int GXB = TILE_X * KX * 2;             // Gx, 16-bit
-  static constexpr int GYB = TILE_Y * KY * 4;             // Gy, TF32
-  static constexpr int BHB = KY * KX * 2;                 // one B_h, 16-bit
+  static constexpr int GYB = TILE_Y * KY * 4;             // Gy, TF32 (shared memory)
+  // B_h is produced as NC column chunks of CK x-pass K-steps (16 columns each) into a ring of
+  // NSLOT chunk slots, each holding the chunk of both images of a pair, with its own full /
+  // empty barriers: generation runs ahead of the x pass by up to NSLOT chunks
+  static constexpr int KS = KX / 16;
+  static constexpr int CK = KS % 4 == 0 ? 4 : KS % 3 == 0 ? 3 : KS % 5 == 0 ? 5 : KS % 2 == 0 ? 2 : 1;
+  static constexpr int NC = KS / CK;
+  static constexpr int CW = 16 * CK;                      // chunk columns
+  static constexpr int CB = KY * CW * 2;                  // bytes of one image's chunk (16-bit)
   static constexpr int FHS = KX + 8;                      // f-halo row stride (bytes)
   static constexpr int FHB = (KY * FHS + 127) / 128 * 128;
   static constexpr int TABW = 512;                        // words per table slot
   static constexpr int TABB = 3 * TABW * 4;               // 3 slots: 256 packed pairs | 256 weights
-  static constexpr int SMEM = GXB + GYB + 2 * BHB + FHB + TABB + 128 + 1024;
-  static constexpr int D1S = (KY + 31) / 32 * 32;         // TMEM columns per x-pass accumulator
-  static constexpr int D2C = 2 * D1S;                     // first y-pass accumulator
+  static constexpr int BARB = 256;
+  static constexpr int FIXED = GYB + FHB + TABB + BARB + 1024;
+  static constexpr int NSLOT0 = (232448 - FIXED) / (2 * CB);
+  static constexpr int NSLOT = NSLOT0 < 2 * NC ? NSLOT0 : 2 * NC;
+  static constexpr int SMEM = FIXED + NSLOT * 2 * CB;
+  // tensor memory: Gx (16-bit pairs, one column per two K elements), two x-pass and two
+  // y-pass accumulators
+  static constexpr int GXC = 0;
+  static constexpr int GXS = (KX / 2 + 31) / 32 * 32;
+  static constexpr int D1S = (KY + 31) / 32 * 32;
+  static constexpr int D1C = GXS;
+  static constexpr int D2C = D1C + 2 * D1S;
   static_assert(D2C + 2 * TILE_Y <= 512, "TMEM columns");
+  static_assert(NSLOT >= NC, "chunk ring");
   static_assert(SMEM <= 232448, "tensor-core tile does not fit in shared memory");
   static_assert(KY <= 256, "x-pass N exceeds one MMA");
+  static_assert(NC * CK == KS, "chunking");
+  static_assert(2 * NSLOT + 6 <= BARB / 8 - 2, "barrier space");
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -142,13 +160,27 @@ __device__ __forceinline__ void mma_ss(uint32_t dtmem, uint64_t da, uint64_t db,
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
       :: "r"(dtmem), "l"(da), "l"(db), "r"(idesc), "r"(accumulate));
 }
+// The issuing warp runs converged (operands stay warp-uniform); one elected lane issues.
+// A from tensor memory, B from shared memory, FP16/BF16 (x pass)
+__device__ __forceinline__ void mma_ts_f16(uint32_t dtmem, uint32_t atmem, uint64_t db, uint32_t idesc,
+                                           uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p, e;\n setp.ne.b32 p, %4, 0;\n elect.sync _|e, 0xffffffff;\n"
+      " @e tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}"
+      :: "r"(dtmem), "r"(atmem), "l"(db), "r"(idesc), "r"(accumulate));
+}
 // A from tensor memory, B from shared memory, TF32 (y pass)
 __device__ __forceinline__ void mma_ts_tf32(uint32_t dtmem, uint32_t atmem, uint64_t db, uint32_t idesc,
                                             uint32_t accumulate) {
   asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}"
+      "{\n .reg .pred p, e;\n setp.ne.b32 p, %4, 0;\n elect.sync _|e, 0xffffffff;\n"
+      " @e tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}"
       :: "r"(dtmem), "r"(atmem), "l"(db), "r"(idesc), "r"(accumulate));
+}
+__device__ __forceinline__ void mma_commit_el(uint64_t* mbar) {
+  asm volatile("{\n .reg .pred e;\n elect.sync _|e, 0xffffffff;\n"
+               " @e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n}"
+               :: "r"(smem_u32(mbar)) : "memory");
 }
 
 __device__ __forceinline__ void mma_commit(uint64_t* mbar) {
@@ -161,17 +193,34 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* mbar) {
                :: "r"(smem_u32(mbar)) : "memory");
 }
 
-// Bounded wait for phase `parity` of an mbarrier.  Gives up (false) after kWaitLimit polls,
-// or early once the CTA's abort flag is raised (when `flag` is given).
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait for phase `parity` of an mbarrier.  Each poll may suspend the thread (up to
+// kSuspendNs, woken early when the phase completes), so waiting warps take no issue slots.
+// Gives up (false) after kWaitLimit polls or kWaitNs of wall time, or early once the CTA's
+// abort flag is raised (when `flag` is given).
+constexpr uint32_t kSuspendNs = 1000000;
+constexpr uint64_t kWaitNs = 2000000000ull;
 __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, const volatile int* flag) {
+  const uint32_t a = smem_u32(mbar);
+  uint64_t t0 = 0;
   for (int it = 0; it < kWaitLimit; ++it) {
     uint32_t done;
     asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
         " selp.u32 %0, 1, 0, p;\n}"
-        : "=r"(done) : "r"(smem_u32(mbar)), "r"(parity) : "memory");
+        : "=r"(done) : "r"(a), "r"(parity), "r"(kSuspendNs) : "memory");
     if (done) return true;
-    if (flag && (it & 63) == 63 && *flag) return false;
+    if ((it & 7) == 7 && flag && *flag) return false;
+    if ((it & 15) == 0) {
+      const uint64_t now = global_ns();
+      if (it == 0) t0 = now;
+      else if (now - t0 > kWaitNs) return false;
+    }
   }
   return false;
 }
@@ -189,6 +238,12 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
         "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
 }
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&r)[8]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};"
+               :: "r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]),
+                  "r"(r[7]) : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -219,14 +274,6 @@ __device__ __forceinline__ void pair_of(int kb, int j, int* k, int* kind) {
   *kind = gp == 0 ? 0 : 1 + ((gp - 1) & 1);   // 0: (1, f-m), 1: cos, 2: sin
 }
 
-// exact (cos, sin)(2 pi n / P) from the plan's two-level tables, n = 128 a + b
-__device__ __forceinline__ float2 phase_cs(const DeviceParams& p, int n) {
-  const int a = n >> 7, b = n & (kTrigLo - 1);
-  const float ca = p.ta[2 * a], sa = p.ta[2 * a + 1];
-  const float cb = p.tb[2 * b], sb = p.tb[2 * b + 1];
-  return make_float2(fmaf(ca, cb, -sa * sb), fmaf(sa, cb, ca * sb));
-}
-
 // Table slot of one pair, over integer intensities v = 0..255: [0, 256) the two operand
 // values packed (first in the low half), [256, 512) the fold weight (FP32 bits).
 template <typename T>
@@ -236,31 +283,43 @@ __device__ __forceinline__ void build_pair_table(const DeviceParams& p, int k, i
   const float fm = (float)v - p.center;
   float a = 1.f, wgt = p.c[0];
   if (kind != 0) {
-    const float2 cs = phase_cs(p, (k * v) % p.P);
-    a = kind == 1 ? cs.x : cs.y;
+    // phase index n = (k v) mod P is exact in integers; 2 n / P is within one ulp
+    float sn, cs;
+    sincospif(2.0f * (float)((k * v) % p.P) * p.invP, &sn, &cs);
+    a = kind == 1 ? cs : sn;
     wgt = p.c[k] * a;
   }
   if (ctid < 256) slot[v] = pack2<T>(a, fm * a);
   else slot[256 + v] = __float_as_uint(wgt);
 }
 
-// Generate one pair over the halo tile into the two B_h buffers (rows = halo rows hy, K =
-// halo columns hx).  Eight consecutive threads fill the eight rows of one core matrix, so
-// the 16-byte stores are conflict-free.  Rows and columns past the halo need only be finite
-// (the matching entries of Gx and Gy are zero); pixels outside the image are zero, tested
-// only on border tiles, with a column bit mask per 8-pixel group.
+// Generate chunk c (halo columns [c CW, (c+1) CW)) of one pair into the chunk slot (rows =
+// halo rows hy, K = halo columns; image a at `dst`, image b at dst + CB).  Eight consecutive
+// threads fill the eight rows of one core matrix, so the 16-byte stores are conflict-free.
+// Rows and columns past the halo need only be finite (the matching entries of Gx and Gy are
+// zero); pixels outside the image are zero, tested only on border tiles, with a column bit
+// mask per 8-pixel group.
 template <int RAD, typename T>
-__device__ __forceinline__ void gen_pair(unsigned char* bh, const unsigned char* fh, const uint32_t* tab,
-                                         bool tile_int, bool interior, int tx0, int ty0, int H, int W,
-                                         const float* __restrict__ in, long long pitch, int k, int kind,
-                                         const DeviceParams& p, int ctid) {
+__device__ __forceinline__ void gen_chunk(unsigned char* dst, int c, const unsigned char* fh, const uint32_t* tab,
+                                          bool tile_int, bool interior, int tx0, int ty0, int H, int W,
+                                          const float* __restrict__ in, long long pitch, int k, int kind,
+                                          const DeviceParams& p, int ctid) {
   using C = TcCfg<RAD>;
-  constexpr int KG = C::KX / 8;
+  constexpr int KG = C::CW / 8;                  // 8-column groups per chunk row
   const int col_lo = max(0, RAD - tx0), col_hi = min(C::HX, W - tx0 + RAD);   // inside: [lo, hi)
+  // item i = 8 g + r7: core-matrix group g = (row block) KG + (column group), row r7 of the
+  // block; its 16-byte store lands at 16 i
+  constexpr int GSTEP = NCT / 8;                 // groups advanced per sweep
+  const int r7 = ctid & 7;
+  int rb = (ctid >> 3) / KG, cx = (ctid >> 3) % KG;
+#pragma unroll 2
   for (int i = ctid; i < C::KY * KG; i += NCT) {
-    const int hy = ((i >> 3) / KG) * 8 + (i & 7);
-    const int hx0 = ((i >> 3) % KG) * 8;
-    const int off = off16<C::KX>(hy, hx0);
+    const int hy = rb * 8 + r7;
+    const int hx0 = (c * KG + cx) * 8;
+    const int off = 16 * i;
+    cx += GSTEP % KG;
+    rb += GSTEP / KG;
+    if (cx >= KG) { cx -= KG; ++rb; }
     if (!tile_int) {
       // general values: read f from global memory, one pixel at a time (16-bit stores)
       const int gy = ty0 - RAD + hy;
@@ -278,8 +337,8 @@ __device__ __forceinline__ void gen_pair(unsigned char* bh, const unsigned char*
           }
         }
         const uint32_t e = pack2<T>(a, fm * a);
-        *reinterpret_cast<unsigned short*>(bh + off + 2 * j) = (unsigned short)(e & 0xFFFFu);
-        *reinterpret_cast<unsigned short*>(bh + C::BHB + off + 2 * j) = (unsigned short)(e >> 16);
+        *reinterpret_cast<unsigned short*>(dst + off + 2 * j) = (unsigned short)(e & 0xFFFFu);
+        *reinterpret_cast<unsigned short*>(dst + C::CB + off + 2 * j) = (unsigned short)(e >> 16);
       }
       continue;
     }
@@ -287,7 +346,7 @@ __device__ __forceinline__ void gen_pair(unsigned char* bh, const unsigned char*
     {
       const uint2 bytes = *reinterpret_cast<const uint2*>(fh + hy * C::FHS + hx0);
 #pragma unroll
-      for (int j = 0; j < 8; ++j) e[j] = tab[((j < 4 ? bytes.x : bytes.y) >> (8 * (j & 3))) & 0xFFu];
+      for (int j = 0; j < 8; ++j) e[j] = tab[__byte_perm(j < 4 ? bytes.x : bytes.y, 0u, 0x4440u | (j & 3))];
       if (!interior) {
         const int gy = ty0 - RAD + hy;
         const bool row_in = hy < C::HY && gy >= 0 && gy < H;
@@ -297,10 +356,10 @@ __device__ __forceinline__ void gen_pair(unsigned char* bh, const unsigned char*
         for (int j = 0; j < 8; ++j) e[j] = ((mask >> j) & 1u) ? e[j] : 0u;
       }
     }
-    *reinterpret_cast<uint4*>(bh + off) =
+    *reinterpret_cast<uint4*>(dst + off) =
         make_uint4(__byte_perm(e[0], e[1], 0x5410), __byte_perm(e[2], e[3], 0x5410),
                    __byte_perm(e[4], e[5], 0x5410), __byte_perm(e[6], e[7], 0x5410));
-    *reinterpret_cast<uint4*>(bh + C::BHB + off) =
+    *reinterpret_cast<uint4*>(dst + C::CB + off) =
         make_uint4(__byte_perm(e[0], e[1], 0x7632), __byte_perm(e[2], e[3], 0x7632),
                    __byte_perm(e[4], e[5], 0x7632), __byte_perm(e[6], e[7], 0x7632));
   }
@@ -313,49 +372,42 @@ fbf_tc_kernel(const __grid_constant__ DeviceParams p, const Work w, const Scratc
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // 1024-byte aligned base, kept as an offset into the shared array (shared address space)
   unsigned char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-  unsigned char* sGx = base;                        // x-pass A operand
-  unsigned char* sGy = sGx + C::GXB;                // y-pass B operand
-  unsigned char* sBh = sGy + C::GYB;                // the pair's two x-pass B operands
-  unsigned char* sFh = sBh + 2 * C::BHB;            // f of the halo tile (uint8)
+  unsigned char* sGy = base;                        // y-pass B operand
+  unsigned char* sBh = sGy + C::GYB;                // chunk ring of the x-pass B operands
+  unsigned char* sFh = sBh + C::NSLOT * 2 * C::CB;  // f of the halo tile (uint8)
   uint32_t* sTab = reinterpret_cast<uint32_t*>(sFh + C::FHB);   // 3 pair-table slots
   uint64_t* bars = reinterpret_cast<uint64_t*>(sTab + 3 * C::TABW);
-  uint64_t* bFull = bars + 0;
-  uint64_t* bXd = bars + 1;
-  uint64_t* bYd = bars + 2;
-  uint64_t* bFd = bars + 3;
-  uint64_t* bDrain = bars + 4;
-  uint32_t* sTmem = reinterpret_cast<uint32_t*>(bars + 5);
+  uint64_t* bXa = bars + 0;            // x pass of the pair's first image complete
+  uint64_t* bXb = bars + 1;            // ... second image
+  uint64_t* bYa = bars + 2;            // y pass of the first image complete
+  uint64_t* bYb = bars + 3;            // ... second image (and so the whole pair)
+  uint64_t* bFd = bars + 4;            // the pair's D2 folded (16 warp arrivals)
+  uint64_t* bDrain = bars + 5;
+  uint64_t* bFull = bars + 6;                  // [NSLOT] chunk generated (16 warp arrivals)
+  uint64_t* bEmpty = bars + 6 + C::NSLOT;      // [NSLOT] chunk consumed (tcgen05.commit)
+  uint32_t* sTmem = reinterpret_cast<uint32_t*>(bars + 6 + 2 * C::NSLOT);
   volatile int* sAbort = reinterpret_cast<volatile int*>(sTmem + 1);
   volatile int* sFin = sAbort + 1;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-  // ---- set-up: Gx (16-bit), Gy (TF32), barriers, TMEM ------------------------------------
-  for (int i = tid; i < TILE_X * (C::KX / 8); i += NTHREADS) {
-    const int o = i / (C::KX / 8), k8 = (i - o * (C::KX / 8)) * 8;
-    float v[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int d = k8 + j - o;   // tap index 0..2r
-      v[j] = (d >= 0 && d <= 2 * RAD) ? p.g[d] : 0.f;
-    }
-    *reinterpret_cast<uint4*>(sGx + off16<C::KX>(o, k8)) =
-        make_uint4(pack2<T>(v[0], v[1]), pack2<T>(v[2], v[3]), pack2<T>(v[4], v[5]), pack2<T>(v[6], v[7]));
-  }
+  // ---- set-up: Gy (TF32, shared memory), barriers, TMEM, Gx (tensor memory) ----------------
   for (int i = tid; i < TILE_Y * (C::KY / 4); i += NTHREADS) {
     const int o = i / (C::KY / 4), k4 = (i - o * (C::KY / 4)) * 4;
     uint32_t v[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      const int d = k4 + j - o;
+      const int d = k4 + j - o;   // tap index 0..2r
       v[j] = to_tf32((d >= 0 && d <= 2 * RAD) ? p.g[d] : 0.f);
     }
     *reinterpret_cast<uint4*>(sGy + off32<C::KY>(o, k4)) = make_uint4(v[0], v[1], v[2], v[3]);
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(bFull)), "r"(NCW));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(bXd)));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(bYd)));
+    for (int i = 0; i < C::NSLOT; ++i) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(bFull + i)), "r"(NCW));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(bEmpty + i)));
+    }
+    for (int i = 0; i < 4; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(bXa + i)));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(bFd)), "r"(NCW));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(bDrain)));
     *sAbort = 0;
@@ -370,6 +422,23 @@ fbf_tc_kernel(const __grid_constant__ DeviceParams p, const Work w, const Scratc
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *sTmem;
+  if (warp < 4) {
+    // Gx[x', hx] = g(hx - x' - r) in lanes x' = 32 warp + lane, two K elements per column
+    const int o = 32 * warp + lane;
+    for (int j0 = 0; j0 < C::KX / 2; j0 += 8) {
+      uint32_t v[8];
+#pragma unroll
+      for (int jj = 0; jj < 8; ++jj) {
+        const int d0 = 2 * (j0 + jj) - o, d1 = d0 + 1;
+        v[jj] = pack2<T>((d0 >= 0 && d0 <= 2 * RAD) ? p.g[d0] : 0.f, (d1 >= 0 && d1 <= 2 * RAD) ? p.g[d1] : 0.f);
+      }
+      tmem_st8(tmem + ((uint32_t)(32 * warp) << 16) + C::GXC + j0, v);
+    }
+    tmem_wait_st();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
 
   // ---- this CTA's share of the weighted (tile, term) sequence --------------------------------
   const SingleSrc src{&p, w};
@@ -385,12 +454,18 @@ fbf_tc_kernel(const __grid_constant__ DeviceParams p, const Work w, const Scratc
 
   if (warp == NCW) {
     // ===================== MMA issuer ======================================================
-    if (lane == 0) {
+    // Issue order per pair: x(a), x(b), y(a), y(b).  Each barrier it waits on completes while
+    // the tensor pipe still holds the previously issued pass, so the pipe does not drain.
+    {
+      // every lane waits; a wait counts as given up when any lane gave up
+      auto wait_all = [&](uint64_t* bar, uint32_t par) { return __all_sync(0xffffffffu, mbar_wait(bar, par, sAbort)); };
       const uint32_t fmt = std::is_same<T, __nv_bfloat16>::value ? 1u : 0u;
       const uint32_t idX = instr_desc(fmt, TILE_X, C::KY);
       const uint32_t idY = instr_desc(2u, TILE_X, TILE_Y);
-      const uint32_t aGx = smem_u32(sGx), aGy = smem_u32(sGy), aBh = smem_u32(sBh);
+      const uint64_t dGy = op_desc(smem_u32(sGy), 32 * C::KY);
+      const uint64_t dBh = op_desc(smem_u32(sBh), 16 * C::CW);
       uint32_t P = 0;
+      int slot0 = 0, ring0 = 0;        // ring slot and use count of the pair's first chunk
       bool ab = false;
       int img = img0;
       long long u = u0;
@@ -400,35 +475,47 @@ fbf_tc_kernel(const __grid_constant__ DeviceParams p, const Work w, const Scratc
         const int ke = (img == img_end && t == u_end / K) ? (int)(u_end - t * K) : K;
         const int np = frag_pairs(kb, ke);
         for (int j = 0; j < np; ++j, ++P) {
-          if (!mbar_wait(bFull, P & 1, sAbort)) { ab = true; break; }
-          if (P > 0 && !mbar_wait(bYd, (P - 1) & 1, sAbort)) { ab = true; break; }   // D1 free
-          tc_fence_after();
 #pragma unroll
           for (int s = 0; s < 2; ++s) {
-#pragma unroll 1
-            for (int ks = 0; ks < C::KX / 16; ++ks)
-              mma_ss(tmem + s * C::D1S, op_desc(aGx + ks * 256, 16 * C::KX),
-                     op_desc(aBh + s * C::BHB + ks * 256, 16 * C::KX), idX, ks > 0);
+            // D1[s] is free once y(s) of the previous pair has completed
+            if (P > 0 && !wait_all(s ? bYb : bYa, (P - 1) & 1)) { ab = true; break; }
+            int sl = slot0, rg = ring0;
+            for (int c = 0; c < C::NC; ++c) {
+              if (s == 0 && !wait_all(bFull + sl, rg & 1)) { ab = true; break; }
+              tc_fence_after();
+#pragma unroll
+              for (int kk = 0; kk < C::CK; ++kk) {
+                const int ks = c * C::CK + kk;
+                mma_ts_f16(tmem + C::D1C + s * C::D1S, tmem + C::GXC + 8 * ks,
+                           dBh + (uint64_t)(((2 * sl + s) * C::CB + kk * 256) >> 4), idX, ks > 0);
+              }
+              if (s == 1) mma_commit_el(bEmpty + sl);   // both images of the chunk consumed
+              if (++sl == C::NSLOT) { sl = 0; ++rg; }
+            }
+            if (ab) break;
+            mma_commit_el(s ? bXb : bXa);
+            if (s == 1) { slot0 = sl; ring0 = rg; }
           }
-          mma_commit(bXd);
-          if (!mbar_wait(bXd, P & 1, sAbort)) { ab = true; break; }
-          if (P > 0 && !mbar_wait(bFd, (P - 1) & 1, sAbort)) { ab = true; break; }   // D2 free
-          tc_fence_after();
+          if (ab) break;
 #pragma unroll
           for (int s = 0; s < 2; ++s) {
-#pragma unroll 1
+            if (!wait_all(s ? bXb : bXa, P & 1)) { ab = true; break; }
+            // D2 is free once the previous pair has been folded
+            if (s == 0 && P > 0 && !wait_all(bFd, (P - 1) & 1)) { ab = true; break; }
+            tc_fence_after();
+#pragma unroll
             for (int ks = 0; ks < C::KY / 8; ++ks)
-              mma_ts_tf32(tmem + C::D2C + s * TILE_Y, tmem + s * C::D1S + 8 * ks,
-                          op_desc(aGy + ks * 256, 32 * C::KY), idY, ks > 0);
+              mma_ts_tf32(tmem + C::D2C + s * TILE_Y, tmem + C::D1C + s * C::D1S + 8 * ks,
+                          dGy + (uint64_t)(16 * ks), idY, ks > 0);
+            mma_commit_el(s ? bYb : bYa);
           }
-          mma_commit(bYd);
         }
         u = t * K + ke;
         if (u >= nunits) { ++img; u = 0; }
       }
-      if (ab) *sAbort = 1;
+      if (ab && lane == 0) *sAbort = 1;
       // every MMA this thread issued has completed before TMEM is released
-      mma_commit(bDrain);
+      mma_commit_el(bDrain);
       mbar_wait(bDrain, 0, nullptr);
     }
     __syncwarp();
@@ -441,13 +528,14 @@ fbf_tc_kernel(const __grid_constant__ DeviceParams p, const Work w, const Scratc
     const float vmax = (float)min(p.R, 255);
     const uint32_t tq = tmem + ((uint32_t)(32 * q) << 16) + C::D2C + PX * rg;
     uint32_t P = 0;
+    int slot = 0, ring = 0;              // ring slot and use count of the next chunk
     bool ab = false;
     int img = img0;
     long long u = u0;
     float nm[PX], dn[PX];
 
     auto fold = [&](uint32_t Pf, int k, int kind, bool tile_int, int tx0, int ty0, const uint32_t* wt) {
-      if (!mbar_wait(bYd, Pf & 1, sAbort)) { ab = true; *sAbort = 1; }
+      if (!mbar_wait(bYb, Pf & 1, sAbort)) { ab = true; *sAbort = 1; }
       tc_fence_after();
       const unsigned char* own = sFh + (oy0 + RAD) * C::FHS + ox + RAD;
 #pragma unroll
@@ -515,16 +603,20 @@ fbf_tc_kernel(const __grid_constant__ DeviceParams p, const Work w, const Scratc
       for (int j = 0; j < np; ++j, ++P) {
         int k, kind;
         pair_of(kb, j, &k, &kind);
-        uint32_t* slot = sTab + (P % 3) * C::TABW;
-        if (tile_int) build_pair_table<T>(p, k, kind, slot, tid);
+        uint32_t* tslot = sTab + (P % 3) * C::TABW;
+        if (tile_int) build_pair_table<T>(p, k, kind, tslot, tid);
         ab = sync_compute_or(ab || *sAbort);   // also publishes the table
         if (ab) break;
-        // B_h is free once the previous pair's x pass has completed
-        if (P > 0 && !mbar_wait(bXd, (P - 1) & 1, sAbort)) { ab = true; *sAbort = 1; }
-        gen_pair<RAD, T>(sBh, sFh, slot, tile_int, interior, tx0, ty0, H, W, w.in, pitch, k, kind, p, tid);
-        proxy_fence();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(bFull);
+        // a ring slot is free once the x pass has consumed the chunk it held NSLOT chunks ago
+        for (int c = 0; c < C::NC; ++c) {
+          if (ring > 0 && !mbar_wait(bEmpty + slot, (ring - 1) & 1, sAbort)) { ab = true; *sAbort = 1; }
+          gen_chunk<RAD, T>(sBh + 2 * slot * C::CB, c, sFh, tslot, tile_int, interior, tx0, ty0, H, W, w.in,
+                            pitch, k, kind, p, tid);
+          proxy_fence();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(bFull + slot);
+          if (++slot == C::NSLOT) { slot = 0; ++ring; }
+        }
         if (j > 0) fold(P - 1, kprev, kindprev, tile_int, tx0, ty0, sTab + ((P - 1) % 3) * C::TABW + 256);
         kprev = k;
         kindprev = kind;
@@ -539,8 +631,8 @@ fbf_tc_kernel(const __grid_constant__ DeviceParams p, const Work w, const Scratc
       bool finish = true;
       if (!(kb == 0 && ke == K)) {
         const int wmine = term_start(ke) - term_start(kb);
-        const int slot = (u0 / K == t && img == img0) ? 0 : 1;
-        float* pp = sc.partial + ((long long)(cta * 2 + slot) * 2) * PX * NCT;
+        const int pslot = (u0 / K == t && img == img0) ? 0 : 1;
+        float* pp = sc.partial + ((long long)(cta * 2 + pslot) * 2) * PX * NCT;
 #pragma unroll
         for (int a = 0; a < PX; ++a) {
           pp[a * NCT + tid] = nm[a];
