@@ -79,8 +79,8 @@ struct TcCfg {
   static constexpr int CB = KY * CW * 2;                  // bytes of one image's chunk (16-bit)
   static constexpr int FHS = KX + 8;                      // f-halo row stride (bytes)
   static constexpr int FHB = (KY * FHS + 127) / 128 * 128;
-  static constexpr int TABW = 512;                        // words per table slot
-  static constexpr int TABB = 3 * TABW * 4;               // 3 slots: 256 packed pairs | 256 weights
+  static constexpr int TABW = 1024;                       // words per term-table slot
+  static constexpr int TABB = 2 * TABW * 4;               // 2 slots (terms k even / odd)
   static constexpr int BARB = 256;
   static constexpr int FIXED = GYB + FHB + TABB + BARB + 1024;
   static constexpr int NSLOT0 = (232448 - FIXED) / (2 * CB);
@@ -274,23 +274,67 @@ __device__ __forceinline__ void pair_of(int kb, int j, int* k, int* kind) {
   *kind = gp == 0 ? 0 : 1 + ((gp - 1) & 1);   // 0: (1, f-m), 1: cos, 2: sin
 }
 
-// Table slot of one pair, over integer intensities v = 0..255: [0, 256) the two operand
-// values packed (first in the low half), [256, 512) the fold weight (FP32 bits).
+// Term-table slot over integer intensities v = 0..255: [0, 256) the cos pair's two operand
+// values packed (first in the low half), [256, 512) the sin pair's, [512, 768) and [768, 1024)
+// their fold weights (FP32 bits).  For k = 0 only the first and third parts are used, with
+// the pair (1, f - m) and the weight c_0.  One sincospif per entry serves both pairs.
 template <typename T>
-__device__ __forceinline__ void build_pair_table(const DeviceParams& p, int k, int kind, uint32_t* slot,
-                                                 int ctid) {
+__device__ __forceinline__ void build_term_table(const DeviceParams& p, int k, uint32_t* slot, int ctid) {
   const int v = ctid & 255;
   const float fm = (float)v - p.center;
-  float a = 1.f, wgt = p.c[0];
-  if (kind != 0) {
-    // phase index n = (k v) mod P is exact in integers; 2 n / P is within one ulp
-    float sn, cs;
-    sincospif(2.0f * (float)((k * v) % p.P) * p.invP, &sn, &cs);
-    a = kind == 1 ? cs : sn;
-    wgt = p.c[k] * a;
+  float cs = 1.f, sn = 0.f;
+  if (k != 0) {
+    // phase index n = (k v) mod P, exact: k v < 2^24 and the float quotient is corrected
+    const int x = k * v;
+    int n = x - (int)floorf((float)x * p.invP) * p.P;
+    n += n < 0 ? p.P : 0;
+    n -= n >= p.P ? p.P : 0;
+    sincospif(2.0f * (float)n * p.invP, &sn, &cs);   // 2 n / P within one ulp
   }
-  if (ctid < 256) slot[v] = pack2<T>(a, fm * a);
-  else slot[256 + v] = __float_as_uint(wgt);
+  if (ctid < 256) {
+    slot[v] = pack2<T>(cs, fm * cs);
+    slot[256 + v] = pack2<T>(sn, fm * sn);
+  } else {
+    const float ck = p.c[k];
+    slot[512 + v] = __float_as_uint(ck * cs);
+    slot[768 + v] = __float_as_uint(ck * sn);
+  }
+}
+
+// General (non-integer or out-of-table) values, one pixel at a time.  Kept out of line so
+// the table paths stay small in the instruction cache.
+template <typename T>
+__device__ __noinline__ void gen_item_slow(unsigned char* dst, int cb, int off, int hy, int hx0, int HY, int HX,
+                                           int gy0, int gx0, int H, int W, const float* __restrict__ in,
+                                           long long pitch, int k, int kind, const DeviceParams& p) {
+  const int gy = gy0 + hy;
+  for (int j = 0; j < 8; ++j) {
+    const int hx = hx0 + j, gx = gx0 + hx;
+    float a = 0.f, fm = 0.f;
+    if (hy < HY && hx < HX && gy >= 0 && gy < H && gx >= 0 && gx < W) {
+      const float fv = __ldg(in + (long long)gy * pitch + gx);
+      fm = fv - p.center;
+      a = 1.f;
+      if (kind != 0) {
+        const float2 cs = term_cs_any((float)k, fv, p);
+        a = kind == 1 ? cs.x : cs.y;
+      }
+    }
+    const uint32_t e = pack2<T>(a, fm * a);
+    *reinterpret_cast<unsigned short*>(dst + off + 2 * j) = (unsigned short)(e & 0xFFFFu);
+    *reinterpret_cast<unsigned short*>(dst + cb + off + 2 * j) = (unsigned short)(e >> 16);
+  }
+}
+
+__device__ __noinline__ float fold_weight_slow(const DeviceParams& p, int k, int kind, const float* __restrict__ in,
+                                               long long pitch, int H, int W, int gy, int gx) {
+  float wgt = p.c[k];
+  if (kind != 0) {
+    const float fv = (gy < H && gx < W) ? __ldg(in + (long long)gy * pitch + gx) : 0.f;
+    const float2 cs = term_cs_any((float)k, fv, p);
+    wgt *= kind == 1 ? cs.x : cs.y;
+  }
+  return wgt;
 }
 
 // Generate chunk c (halo columns [c CW, (c+1) CW)) of one pair into the chunk slot (rows =
@@ -321,25 +365,7 @@ __device__ __forceinline__ void gen_chunk(unsigned char* dst, int c, const unsig
     rb += GSTEP / KG;
     if (cx >= KG) { cx -= KG; ++rb; }
     if (!tile_int) {
-      // general values: read f from global memory, one pixel at a time (16-bit stores)
-      const int gy = ty0 - RAD + hy;
-#pragma unroll 1
-      for (int j = 0; j < 8; ++j) {
-        const int hx = hx0 + j, gx = tx0 - RAD + hx;
-        float a = 0.f, fm = 0.f;
-        if (hy < C::HY && hx < C::HX && gy >= 0 && gy < H && gx >= 0 && gx < W) {
-          const float fv = __ldg(in + (long long)gy * pitch + gx);
-          fm = fv - p.center;
-          a = 1.f;
-          if (kind != 0) {
-            const float2 cs = term_cs_any((float)k, fv, p);
-            a = kind == 1 ? cs.x : cs.y;
-          }
-        }
-        const uint32_t e = pack2<T>(a, fm * a);
-        *reinterpret_cast<unsigned short*>(dst + off + 2 * j) = (unsigned short)(e & 0xFFFFu);
-        *reinterpret_cast<unsigned short*>(dst + C::CB + off + 2 * j) = (unsigned short)(e >> 16);
-      }
+      gen_item_slow<T>(dst, C::CB, off, hy, hx0, C::HY, C::HX, ty0 - RAD, tx0 - RAD, H, W, in, pitch, k, kind, p);
       continue;
     }
     uint32_t e[8];
@@ -375,8 +401,8 @@ fbf_tc_kernel(const __grid_constant__ DeviceParams p, const Work w, const Scratc
   unsigned char* sGy = base;                        // y-pass B operand
   unsigned char* sBh = sGy + C::GYB;                // chunk ring of the x-pass B operands
   unsigned char* sFh = sBh + C::NSLOT * 2 * C::CB;  // f of the halo tile (uint8)
-  uint32_t* sTab = reinterpret_cast<uint32_t*>(sFh + C::FHB);   // 3 pair-table slots
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sTab + 3 * C::TABW);
+  uint32_t* sTab = reinterpret_cast<uint32_t*>(sFh + C::FHB);   // 2 term-table slots
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sTab + 2 * C::TABW);
   uint64_t* bXa = bars + 0;            // x pass of the pair's first image complete
   uint64_t* bXb = bars + 1;            // ... second image
   uint64_t* bYa = bars + 2;            // y pass of the first image complete
@@ -534,33 +560,31 @@ fbf_tc_kernel(const __grid_constant__ DeviceParams p, const Work w, const Scratc
     long long u = u0;
     float nm[PX], dn[PX];
 
+    auto wtab = [&](int k, int kind) { return sTab + (k & 1) * C::TABW + 512 + (kind == 2 ? 256 : 0); };
+    // own pixels' weights for rows h .. h + 7 (table path: the pair's weight table)
+    auto weights8 = [&](int h, int k, int kind, bool tile_int, int tx0, int ty0, const uint32_t* wt, float (&wv)[8]) {
+      const unsigned char* own = sFh + (oy0 + RAD + h) * C::FHS + ox + RAD;
+#pragma unroll
+      for (int ii = 0; ii < 8; ++ii)
+        wv[ii] = tile_int ? __uint_as_float(wt[own[ii * C::FHS]])
+                          : fold_weight_slow(p, k, kind, w.in, pitch, H, W, ty0 + oy0 + h + ii, tx0 + ox);
+    };
     auto fold = [&](uint32_t Pf, int k, int kind, bool tile_int, int tx0, int ty0, const uint32_t* wt) {
+      float wv[8];
+      weights8(0, k, kind, tile_int, tx0, ty0, wt, wv);   // before the wait: off the critical path
       if (!mbar_wait(bYb, Pf & 1, sAbort)) { ab = true; *sAbort = 1; }
       tc_fence_after();
-      const unsigned char* own = sFh + (oy0 + RAD) * C::FHS + ox + RAD;
 #pragma unroll
       for (int h = 0; h < PX; h += 8) {   // 8 rows at a time keeps the live registers low
         uint32_t a[8], b[8];
         tmem_ld8(tq + h, a);
         tmem_ld8(tq + TILE_Y + h, b);
+        if (h > 0) weights8(h, k, kind, tile_int, tx0, ty0, wt, wv);
         tmem_wait_ld();
 #pragma unroll
         for (int ii = 0; ii < 8; ++ii) {
-          const int i = h + ii;
-          float wgt;
-          if (tile_int) {
-            wgt = __uint_as_float(wt[own[i * C::FHS]]);
-          } else {
-            wgt = p.c[k];
-            if (kind != 0) {
-              const int gy = ty0 + oy0 + i, gx = tx0 + ox;
-              const float fv = (gy < H && gx < W) ? __ldg(w.in + (long long)gy * pitch + gx) : 0.f;
-              const float2 cs = term_cs_any((float)k, fv, p);
-              wgt *= kind == 1 ? cs.x : cs.y;
-            }
-          }
-          dn[i] = fmaf(wgt, __uint_as_float(a[ii]), dn[i]);
-          nm[i] = fmaf(wgt, __uint_as_float(b[ii]), nm[i]);
+          dn[h + ii] = fmaf(wv[ii], __uint_as_float(a[ii]), dn[h + ii]);
+          nm[h + ii] = fmaf(wv[ii], __uint_as_float(b[ii]), nm[h + ii]);
         }
       }
       tc_fence_before();
@@ -579,6 +603,7 @@ fbf_tc_kernel(const __grid_constant__ DeviceParams p, const Work w, const Scratc
       // f of the tile + halo as bytes (zero outside the image and in the padding); the tile
       // takes the table path when every pixel is an integer in [0, min(R, 255)]
       int ok = 1;
+#pragma unroll 4
       for (int i = tid; i < C::KY * C::FHS / 4; i += NCT) {
         const int hy = (4 * i) / C::FHS, hx = 4 * i - hy * C::FHS;
         const int gy = ty0 - RAD + hy;
@@ -603,8 +628,10 @@ fbf_tc_kernel(const __grid_constant__ DeviceParams p, const Work w, const Scratc
       for (int j = 0; j < np; ++j, ++P) {
         int k, kind;
         pair_of(kb, j, &k, &kind);
-        uint32_t* tslot = sTab + (P % 3) * C::TABW;
-        if (tile_int) build_pair_table<T>(p, k, kind, tslot, tid);
+        // the term's tables are built at its first pair; slot k & 1 is free by then (its
+        // previous term was last read by a fold before the previous pair's barrier)
+        uint32_t* tslot = sTab + (k & 1) * C::TABW + (kind == 2 ? 256 : 0);
+        if (tile_int && kind != 2) build_term_table<T>(p, k, sTab + (k & 1) * C::TABW, tid);
         ab = sync_compute_or(ab || *sAbort);   // also publishes the table
         if (ab) break;
         // a ring slot is free once the x pass has consumed the chunk it held NSLOT chunks ago
@@ -617,13 +644,13 @@ fbf_tc_kernel(const __grid_constant__ DeviceParams p, const Work w, const Scratc
           if (lane == 0) mbar_arrive(bFull + slot);
           if (++slot == C::NSLOT) { slot = 0; ++ring; }
         }
-        if (j > 0) fold(P - 1, kprev, kindprev, tile_int, tx0, ty0, sTab + ((P - 1) % 3) * C::TABW + 256);
+        if (j > 0) fold(P - 1, kprev, kindprev, tile_int, tx0, ty0, wtab(kprev, kindprev));
         kprev = k;
         kindprev = kind;
       }
       // last pair (also on abort, where its bounded wait returns at once: every lane of a warp
       // must reach the fold's __syncwarp)
-      fold(P - 1, kprev, kindprev, tile_int, tx0, ty0, sTab + ((P - 1) % 3) * C::TABW + 256);
+      fold(P - 1, kprev, kindprev, tile_int, tx0, ty0, wtab(kprev, kindprev));
       ab = sync_compute_or(ab || *sAbort);
       if (ab) break;
 
