@@ -79,6 +79,14 @@ def _fp32_peak_tflops(sm_count: int) -> tuple[float, str]:
     return sm_count * 128 * 2 * mhz * 1e6 / 1e12, f"{sm_count} SMs x 128 FP32 lanes x 2 flop x {mhz:.0f} MHz ({src})"
 
 
+def _bf16_peak() -> float:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["bf16_tflops"])
+    except Exception:
+        return 1900.0   # fallback figure for this GPU when the measured file is absent
+
+
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -137,18 +145,35 @@ class ClockSampler:
                 "samples": len(rows), "window": "warm-up + timed region (50 ms sampling)"}
 
 
-def _traffic_for(kernel_file: str):
-    """Per-launch DRAM bytes from the committed ncu summary, if it was taken on the
-    current kernel source; else None."""
+def _sources_sha(files) -> str:
+    h = hashlib.sha256()
+    for f in files:
+        h.update(open(os.path.join(ROOT, "paper_1811_02168_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
+def _traffic_for(kernel: str):
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if it was taken on
+    the current kernel sources; else None."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
-            t = json.load(fh)
-        src = open(os.path.join(ROOT, "paper_1811_02168_gb300", "csrc", kernel_file), "rb").read()
-        if t.get("kernel_sha256") == hashlib.sha256(src).hexdigest():
+            t = json.load(fh)[kernel]
+        if t.get("sources_sha256") == _sources_sha(t["sources"]):
             return t
     except Exception:
         pass
     return None
+
+
+def _tc_mma_flops(K: int, r: int, H: int, W: int) -> float:
+    """FP16-equivalent dense MMA flops one tensor-core launch executes (banded Toeplitz
+    contractions, padding included; the TF32 y pass counts twice, at half the FP16 rate)."""
+    R = 6 if r <= 6 else 15 if r <= 15 else 30
+    kx = (128 + 2 * R + 15) // 16 * 16
+    ky = (64 + 2 * R + 15) // 16 * 16
+    tiles = math.ceil(W / 128) * math.ceil(H / 64)
+    per_image = 2 * 128 * ky * kx + 2 * (2 * 128 * 64 * ky)
+    return tiles * (4 * K - 2) * per_image
 
 
 _ORACLE_PLANS = {}
@@ -326,7 +351,7 @@ def run_ours(a):
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     peak, peak_src = _fp32_peak_tflops(sm_count)
     achieved = sum(flops) / (sum(launch_ms) / 1e3) / 1e12
-    tr = _traffic_for("fbf_fp32.cu")
+    tr = _traffic_for("fbf_fp32_kernel")
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": None, "kernel": "fbf_fp32_kernel",
             "peak_source": peak_src + " (derived FP32 FFMA peak)",
@@ -351,8 +376,10 @@ def run_ours(a):
         cpu_px = 0
         cpu_s = 0.0
         errs = []
+        refs = []
         for i, j in enumerate(jobs):
             ref, dt = _oracle_band(imgs_np[j.seed], j, a.cpu_rows)
+            refs.append(ref)
             cpu_s += dt
             cpu_px += ref.shape[0] * j.W
             got = outs[i][: ref.shape[0]].cpu().numpy()
@@ -363,11 +390,68 @@ def run_ours(a):
                       f"image for each sigma; single-threaded NumPy"}
         result["error_vs_oracle"] = {"max_abs": max(errs), "per_image": errs, "tolerance": TOL_FP32,
                                      "sample": f"first {a.cpu_rows} rows of each output"}
+        result["forms"] = _forms(a, B, jobs, plans, x, launch_ms, refs, flush, stream, dev)
+        result["forms"]["fp32"]["max_abs_err"] = max(errs)
     if rank == 0:
         print(json.dumps(result), flush=True)
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+TOL_TC = 0.5   # the stated max-abs bound for the 16-bit channel-stack forms (gray levels)
+
+
+def _forms(a, B, jobs, plans, x, fp32_launch_ms, refs, flush, stream, dev):
+    """The precision forms on the same workload: Mpix/s (kernel time, L2 flushed before each
+    step) and max abs error against the same oracle rows as the FP32 line.  The tensor-core
+    forms take r <= 30."""
+    import numpy as np
+    import torch
+    px = sum(j.H * j.W for j in jobs)
+    fp32_ms = sum(fp32_launch_ms)
+    forms = {"fp32": {"mpix_s": px / (fp32_ms / 1e3) / 1e6, "kernel_ms": fp32_ms,
+                      "max_abs_err": None, "tolerance": TOL_FP32}}
+    steps = max(3, min(a.steps, 20))
+    for name, prec in (("fp16_tc", B.FBF_FP16_TC), ("bf16_tc", B.FBF_BF16_TC)):
+        if any(p.radius > 30 for p in plans):
+            forms[name] = {"unavailable": "radius above 30"}
+            continue
+        tp = [B.Plan(j.sigma, 255, j.theta, K=j.K or 0, eps=j.eps or 0.0, precision=prec) for j in jobs]
+        ys = [torch.empty((j.H, j.W), dtype=torch.float32, device=dev) for j in jobs]
+        sh = stream.cuda_stream
+
+        def run():
+            for p, j, y in zip(tp, jobs, ys):
+                B.fbf_filter(p.handle, x[j.seed].data_ptr(), y.data_ptr(), j.H, j.W, j.W, sh)
+        for _ in range(3):
+            flush.zero_()
+            run()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for e0, e1 in evs:
+            flush.zero_()
+            e0.record(stream)
+            run()
+            e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = statistics.mean(e0.elapsed_time(e1) for e0, e1 in evs)
+        errs = [float(np.abs(y[: r.shape[0]].cpu().numpy() - r).max()) for y, r in zip(ys, refs)]
+        peak = _bf16_peak()
+        alg = sum(_flops_per_px(p.K, p.radius) * j.H * j.W for p, j in zip(tp, jobs)) / (ms / 1e3) / 1e12
+        dense = sum(_tc_mma_flops(p.K, p.radius, j.H, j.W) for p, j in zip(tp, jobs)) / (ms / 1e3) / 1e12
+        tr = _traffic_for("fbf_tc_kernel")
+        forms[name] = {"mpix_s": px / (ms / 1e3) / 1e6, "kernel_ms": ms, "max_abs_err": max(errs),
+                       "per_image_err": errs, "tolerance": TOL_TC, "meets_tolerance": max(errs) <= TOL_TC,
+                       "speedup_vs_fp32": fp32_ms / ms, "kernel": "fbf_tc_kernel",
+                       "roofline": {"bound": "tensor", "unit": "TFLOP/s", "peak": peak,
+                                    "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst, measured)",
+                                    "achieved_algorithmic": alg, "frac_algorithmic": alg / peak,
+                                    "achieved_dense_mma": dense, "frac_dense_mma": dense / peak,
+                                    "traffic": (tr or {}).get("workloads", {}).get(_jobs(a.workload)[0])},
+                       "device_errors": B.fbf_device_errors(True)}
+        for p in tp:
+            p.close()
+    return forms
 
 
 def run_batch(a):

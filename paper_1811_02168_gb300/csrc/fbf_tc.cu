@@ -62,30 +62,42 @@ constexpr int NTHREADS = NCT + 32;      // + the MMA-issuing warp
 constexpr int PX = TILE_Y / 4;          // output pixels per compute thread (one column)
 constexpr int kWaitLimit = 1 << 22;
 
-template <int RAD>
+// FBF_BF16_TC stores every operand value and every x-pass tap as a compensated pair of BF16
+// numbers (hi + lo, lo = the rounding error of hi); the x pass accumulates Gx_hi B_hi +
+// Gx_hi B_lo + Gx_lo B_hi (the lo x lo product is below the FP32 accumulation error),
+// which keeps about 16 significant bits.  FBF_FP16_TC stores one FP16 value per operand.
+template <typename T>
+struct Parts { static constexpr int value = std::is_same<T, __nv_bfloat16>::value ? 2 : 1; };
+
+template <int RAD, int NPART>
 struct TcCfg {
   static constexpr int HX = TILE_X + 2 * RAD;             // halo columns
   static constexpr int KX = (HX + 15) / 16 * 16;          // x-pass K
   static constexpr int HY = TILE_Y + 2 * RAD;             // halo rows
   static constexpr int KY = (HY + 15) / 16 * 16;          // x-pass N = y-pass K
   static constexpr int GYB = TILE_Y * KY * 4;             // Gy, TF32 (shared memory)
+  static constexpr int GLB = NPART == 2 ? TILE_X * KX * 2 : 0;   // Gx_lo (shared memory)
   // B_h is produced as NC column chunks of CK x-pass K-steps (16 columns each) into a ring of
-  // NSLOT chunk slots, each holding the chunk of both images of a pair, with its own full /
-  // empty barriers: generation runs ahead of the x pass by up to NSLOT chunks
+  // NSLOT chunk slots, each holding the chunk of both images of a pair (and of both parts of
+  // the compensated form), with its own full / empty barriers: generation runs ahead of the
+  // x pass by up to NSLOT chunks
   static constexpr int KS = KX / 16;
-  static constexpr int CK = KS % 4 == 0 ? 4 : KS % 3 == 0 ? 3 : KS % 5 == 0 ? 5 : KS % 2 == 0 ? 2 : 1;
+  static constexpr int CK = NPART == 1 ? (KS % 4 == 0 ? 4 : KS % 3 == 0 ? 3 : KS % 5 == 0 ? 5 : KS % 2 == 0 ? 2 : 1)
+                                       : (KS % 2 == 0 ? 2 : KS % 3 == 0 ? 3 : 1);
   static constexpr int NC = KS / CK;
   static constexpr int CW = 16 * CK;                      // chunk columns
-  static constexpr int CB = KY * CW * 2;                  // bytes of one image's chunk (16-bit)
+  static constexpr int CB = KY * CW * 2;                  // bytes of one image part's chunk (16-bit)
+  static constexpr int SLOTB = 2 * NPART * CB;            // a chunk slot: [a, b] per part
   static constexpr int FHS = KX + 8;                      // f-halo row stride (bytes)
   static constexpr int FHB = (KY * FHS + 127) / 128 * 128;
-  static constexpr int TABW = 1024;                       // words per term-table slot
+  static constexpr int GENW = 256 * NPART;                // words of one pair's operand table
+  static constexpr int TABW = 2 * GENW + 512;             // words per term-table slot
   static constexpr int TABB = 2 * TABW * 4;               // 2 slots (terms k even / odd)
   static constexpr int BARB = 256;
-  static constexpr int FIXED = GYB + FHB + TABB + BARB + 1024;
-  static constexpr int NSLOT0 = (232448 - FIXED) / (2 * CB);
+  static constexpr int FIXED = GYB + GLB + FHB + TABB + BARB + 1024;
+  static constexpr int NSLOT0 = (232448 - FIXED) / SLOTB;
   static constexpr int NSLOT = NSLOT0 < 2 * NC ? NSLOT0 : 2 * NC;
-  static constexpr int SMEM = FIXED + NSLOT * 2 * CB;
+  static constexpr int SMEM = FIXED + NSLOT * SLOTB;
   // tensor memory: Gx (16-bit pairs, one column per two K elements), two x-pass and two
   // y-pass accumulators
   static constexpr int GXC = 0;
@@ -94,11 +106,11 @@ struct TcCfg {
   static constexpr int D1C = GXS;
   static constexpr int D2C = D1C + 2 * D1S;
   static_assert(D2C + 2 * TILE_Y <= 512, "TMEM columns");
-  static_assert(NSLOT >= NC, "chunk ring");
+  static_assert(NSLOT >= 1, "chunk ring");
   static_assert(SMEM <= 232448, "tensor-core tile does not fit in shared memory");
   static_assert(KY <= 256, "x-pass N exceeds one MMA");
   static_assert(NC * CK == KS, "chunking");
-  static_assert(2 * NSLOT + 6 <= BARB / 8 - 2, "barrier space");
+  static_assert(2 * NSLOT + 8 <= BARB / 8 - 2, "barrier space");
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -146,6 +158,23 @@ __device__ __forceinline__ uint32_t pack2<__nv_bfloat16>(float a, float b) {
   return *reinterpret_cast<const uint32_t*>(&h);
 }
 
+template <typename T>
+__device__ __forceinline__ float round16(float x);
+template <>
+__device__ __forceinline__ float round16<__half>(float x) { return __half2float(__float2half_rn(x)); }
+template <>
+__device__ __forceinline__ float round16<__nv_bfloat16>(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
+// operand words of one pixel of a pair (values a, b): the packed pair, and for the
+// compensated form the packed pair of rounding errors
+template <typename T, int NPART>
+__device__ __forceinline__ uint2 pair_words(float a, float b) {
+  uint2 r;
+  r.x = pack2<T>(a, b);
+  r.y = NPART == 2 ? pack2<T>(a - round16<T>(a), b - round16<T>(b)) : 0u;
+  return r;
+}
+
 __device__ __forceinline__ uint32_t to_tf32(float x) {
   uint32_t r;
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
@@ -176,6 +205,14 @@ __device__ __forceinline__ void mma_ts_tf32(uint32_t dtmem, uint32_t atmem, uint
       "{\n .reg .pred p, e;\n setp.ne.b32 p, %4, 0;\n elect.sync _|e, 0xffffffff;\n"
       " @e tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}"
       :: "r"(dtmem), "r"(atmem), "l"(db), "r"(idesc), "r"(accumulate));
+}
+// A and B from shared memory, FP16/BF16 (the Gx_lo term of the compensated x pass)
+__device__ __forceinline__ void mma_ss_el(uint32_t dtmem, uint64_t da, uint64_t db, uint32_t idesc,
+                                          uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p, e;\n setp.ne.b32 p, %4, 0;\n elect.sync _|e, 0xffffffff;\n"
+      " @e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
+      :: "r"(dtmem), "l"(da), "l"(db), "r"(idesc), "r"(accumulate));
 }
 __device__ __forceinline__ void mma_commit_el(uint64_t* mbar) {
   asm volatile("{\n .reg .pred e;\n elect.sync _|e, 0xffffffff;\n"
@@ -274,12 +311,14 @@ __device__ __forceinline__ void pair_of(int kb, int j, int* k, int* kind) {
   *kind = gp == 0 ? 0 : 1 + ((gp - 1) & 1);   // 0: (1, f-m), 1: cos, 2: sin
 }
 
-// Term-table slot over integer intensities v = 0..255: [0, 256) the cos pair's two operand
-// values packed (first in the low half), [256, 512) the sin pair's, [512, 768) and [768, 1024)
-// their fold weights (FP32 bits).  For k = 0 only the first and third parts are used, with
-// the pair (1, f - m) and the weight c_0.  One sincospif per entry serves both pairs.
-template <typename T>
+// Term-table slot over integer intensities v = 0..255: [0, GENW) the cos pair's operand
+// words (the two values packed, first in the low half; for the compensated form followed
+// by the packed rounding errors), [GENW, 2 GENW) the sin pair's, then the two fold weight
+// tables (FP32 bits).  For k = 0 only the cos parts are used, holding the pair (1, f - m)
+// and the weight c_0.  One sincospif per entry serves both pairs.
+template <typename T, int NPART>
 __device__ __forceinline__ void build_term_table(const DeviceParams& p, int k, uint32_t* slot, int ctid) {
+  constexpr int GENW = 256 * NPART;
   const int v = ctid & 255;
   const float fm = (float)v - p.center;
   float cs = 1.f, sn = 0.f;
@@ -292,18 +331,24 @@ __device__ __forceinline__ void build_term_table(const DeviceParams& p, int k, u
     sincospif(2.0f * (float)n * p.invP, &sn, &cs);   // 2 n / P within one ulp
   }
   if (ctid < 256) {
-    slot[v] = pack2<T>(cs, fm * cs);
-    slot[256 + v] = pack2<T>(sn, fm * sn);
+    const uint2 wc = pair_words<T, NPART>(cs, fm * cs), ws = pair_words<T, NPART>(sn, fm * sn);
+    if (NPART == 1) {
+      slot[v] = wc.x;
+      slot[GENW + v] = ws.x;
+    } else {
+      reinterpret_cast<uint2*>(slot)[v] = wc;
+      reinterpret_cast<uint2*>(slot + GENW)[v] = ws;
+    }
   } else {
     const float ck = p.c[k];
-    slot[512 + v] = __float_as_uint(ck * cs);
-    slot[768 + v] = __float_as_uint(ck * sn);
+    slot[2 * GENW + v] = __float_as_uint(ck * cs);
+    slot[2 * GENW + 256 + v] = __float_as_uint(ck * sn);
   }
 }
 
 // General (non-integer or out-of-table) values, one pixel at a time.  Kept out of line so
 // the table paths stay small in the instruction cache.
-template <typename T>
+template <typename T, int NPART>
 __device__ __noinline__ void gen_item_slow(unsigned char* dst, int cb, int off, int hy, int hx0, int HY, int HX,
                                            int gy0, int gx0, int H, int W, const float* __restrict__ in,
                                            long long pitch, int k, int kind, const DeviceParams& p) {
@@ -320,9 +365,13 @@ __device__ __noinline__ void gen_item_slow(unsigned char* dst, int cb, int off, 
         a = kind == 1 ? cs.x : cs.y;
       }
     }
-    const uint32_t e = pack2<T>(a, fm * a);
-    *reinterpret_cast<unsigned short*>(dst + off + 2 * j) = (unsigned short)(e & 0xFFFFu);
-    *reinterpret_cast<unsigned short*>(dst + cb + off + 2 * j) = (unsigned short)(e >> 16);
+    const uint2 e = pair_words<T, NPART>(a, fm * a);
+    *reinterpret_cast<unsigned short*>(dst + off + 2 * j) = (unsigned short)(e.x & 0xFFFFu);
+    *reinterpret_cast<unsigned short*>(dst + cb + off + 2 * j) = (unsigned short)(e.x >> 16);
+    if (NPART == 2) {
+      *reinterpret_cast<unsigned short*>(dst + 2 * cb + off + 2 * j) = (unsigned short)(e.y & 0xFFFFu);
+      *reinterpret_cast<unsigned short*>(dst + 3 * cb + off + 2 * j) = (unsigned short)(e.y >> 16);
+    }
   }
 }
 
@@ -348,7 +397,8 @@ __device__ __forceinline__ void gen_chunk(unsigned char* dst, int c, const unsig
                                           bool tile_int, bool interior, int tx0, int ty0, int H, int W,
                                           const float* __restrict__ in, long long pitch, int k, int kind,
                                           const DeviceParams& p, int ctid) {
-  using C = TcCfg<RAD>;
+  constexpr int NPART = Parts<T>::value;
+  using C = TcCfg<RAD, NPART>;
   constexpr int KG = C::CW / 8;                  // 8-column groups per chunk row
   const int col_lo = max(0, RAD - tx0), col_hi = min(C::HX, W - tx0 + RAD);   // inside: [lo, hi)
   // item i = 8 g + r7: core-matrix group g = (row block) KG + (column group), row r7 of the
@@ -365,42 +415,49 @@ __device__ __forceinline__ void gen_chunk(unsigned char* dst, int c, const unsig
     rb += GSTEP / KG;
     if (cx >= KG) { cx -= KG; ++rb; }
     if (!tile_int) {
-      gen_item_slow<T>(dst, C::CB, off, hy, hx0, C::HY, C::HX, ty0 - RAD, tx0 - RAD, H, W, in, pitch, k, kind, p);
+      gen_item_slow<T, NPART>(dst, C::CB, off, hy, hx0, C::HY, C::HX, ty0 - RAD, tx0 - RAD, H, W, in, pitch, k,
+                              kind, p);
       continue;
     }
-    uint32_t e[8];
-    {
-      const uint2 bytes = *reinterpret_cast<const uint2*>(fh + hy * C::FHS + hx0);
-#pragma unroll
-      for (int j = 0; j < 8; ++j) e[j] = tab[__byte_perm(j < 4 ? bytes.x : bytes.y, 0u, 0x4440u | (j & 3))];
-      if (!interior) {
-        const int gy = ty0 - RAD + hy;
-        const bool row_in = hy < C::HY && gy >= 0 && gy < H;
-        const int a = min(8, max(0, col_lo - hx0)), b = min(8, max(0, col_hi - hx0));
-        const unsigned mask = row_in && b > a ? (((1u << b) - 1u) & ~((1u << a) - 1u)) : 0u;
-#pragma unroll
-        for (int j = 0; j < 8; ++j) e[j] = ((mask >> j) & 1u) ? e[j] : 0u;
-      }
+    unsigned mask = 0xFFu;
+    if (!interior) {
+      const int gy = ty0 - RAD + hy;
+      const bool row_in = hy < C::HY && gy >= 0 && gy < H;
+      const int a = min(8, max(0, col_lo - hx0)), b = min(8, max(0, col_hi - hx0));
+      mask = row_in && b > a ? (((1u << b) - 1u) & ~((1u << a) - 1u)) : 0u;
     }
-    *reinterpret_cast<uint4*>(dst + off) =
-        make_uint4(__byte_perm(e[0], e[1], 0x5410), __byte_perm(e[2], e[3], 0x5410),
-                   __byte_perm(e[4], e[5], 0x5410), __byte_perm(e[6], e[7], 0x5410));
-    *reinterpret_cast<uint4*>(dst + C::CB + off) =
-        make_uint4(__byte_perm(e[0], e[1], 0x7632), __byte_perm(e[2], e[3], 0x7632),
-                   __byte_perm(e[4], e[5], 0x7632), __byte_perm(e[6], e[7], 0x7632));
+    const uint2 bytes = *reinterpret_cast<const uint2*>(fh + hy * C::FHS + hx0);
+#pragma unroll
+    for (int h = 0; h < NPART; ++h) {   // the value words, then (compensated form) the error words
+      uint32_t e[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const uint32_t v = __byte_perm(j < 4 ? bytes.x : bytes.y, 0u, 0x4440u | (j & 3));
+        e[j] = tab[NPART * v + h];
+        if (!interior) e[j] = ((mask >> j) & 1u) ? e[j] : 0u;
+      }
+      *reinterpret_cast<uint4*>(dst + 2 * h * C::CB + off) =
+          make_uint4(__byte_perm(e[0], e[1], 0x5410), __byte_perm(e[2], e[3], 0x5410),
+                     __byte_perm(e[4], e[5], 0x5410), __byte_perm(e[6], e[7], 0x5410));
+      *reinterpret_cast<uint4*>(dst + (2 * h + 1) * C::CB + off) =
+          make_uint4(__byte_perm(e[0], e[1], 0x7632), __byte_perm(e[2], e[3], 0x7632),
+                     __byte_perm(e[4], e[5], 0x7632), __byte_perm(e[6], e[7], 0x7632));
+    }
   }
 }
 
 template <int RAD, typename T>
 __global__ void __launch_bounds__(NTHREADS, 1)
 fbf_tc_kernel(const __grid_constant__ DeviceParams p, const Work w, const Scratch sc) {
-  using C = TcCfg<RAD>;
+  constexpr int NPART = Parts<T>::value;
+  using C = TcCfg<RAD, NPART>;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // 1024-byte aligned base, kept as an offset into the shared array (shared address space)
   unsigned char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   unsigned char* sGy = base;                        // y-pass B operand
-  unsigned char* sBh = sGy + C::GYB;                // chunk ring of the x-pass B operands
-  unsigned char* sFh = sBh + C::NSLOT * 2 * C::CB;  // f of the halo tile (uint8)
+  unsigned char* sGl = sGy + C::GYB;                // Gx_lo (compensated form)
+  unsigned char* sBh = sGl + C::GLB;                // chunk ring of the x-pass B operands
+  unsigned char* sFh = sBh + C::NSLOT * C::SLOTB;   // f of the halo tile (uint8)
   uint32_t* sTab = reinterpret_cast<uint32_t*>(sFh + C::FHB);   // 2 term-table slots
   uint64_t* bars = reinterpret_cast<uint64_t*>(sTab + 2 * C::TABW);
   uint64_t* bXa = bars + 0;            // x pass of the pair's first image complete
@@ -409,9 +466,11 @@ fbf_tc_kernel(const __grid_constant__ DeviceParams p, const Work w, const Scratc
   uint64_t* bYb = bars + 3;            // ... second image (and so the whole pair)
   uint64_t* bFd = bars + 4;            // the pair's D2 folded (16 warp arrivals)
   uint64_t* bDrain = bars + 5;
-  uint64_t* bFull = bars + 6;                  // [NSLOT] chunk generated (16 warp arrivals)
-  uint64_t* bEmpty = bars + 6 + C::NSLOT;      // [NSLOT] chunk consumed (tcgen05.commit)
-  uint32_t* sTmem = reinterpret_cast<uint32_t*>(bars + 6 + 2 * C::NSLOT);
+  uint64_t* bRa = bars + 6;            // D1 of the first image rounded to TF32 (16 warp arrivals)
+  uint64_t* bRb = bars + 7;            // ... second image
+  uint64_t* bFull = bars + 8;                  // [NSLOT] chunk generated (16 warp arrivals)
+  uint64_t* bEmpty = bars + 8 + C::NSLOT;      // [NSLOT] chunk consumed (tcgen05.commit)
+  uint32_t* sTmem = reinterpret_cast<uint32_t*>(bars + 8 + 2 * C::NSLOT);
   volatile int* sAbort = reinterpret_cast<volatile int*>(sTmem + 1);
   volatile int* sFin = sAbort + 1;
 
@@ -428,6 +487,20 @@ fbf_tc_kernel(const __grid_constant__ DeviceParams p, const Work w, const Scratc
     }
     *reinterpret_cast<uint4*>(sGy + off32<C::KY>(o, k4)) = make_uint4(v[0], v[1], v[2], v[3]);
   }
+  if (NPART == 2) {
+    for (int i = tid; i < TILE_X * (C::KX / 8); i += NTHREADS) {
+      const int o = i / (C::KX / 8), k8 = (i - o * (C::KX / 8)) * 8;
+      float v[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int d = k8 + j - o;
+        const float gv = (d >= 0 && d <= 2 * RAD) ? p.g[d] : 0.f;
+        v[j] = gv - round16<T>(gv);
+      }
+      *reinterpret_cast<uint4*>(sGl + off16<C::KX>(o, k8)) =
+          make_uint4(pack2<T>(v[0], v[1]), pack2<T>(v[2], v[3]), pack2<T>(v[4], v[5]), pack2<T>(v[6], v[7]));
+    }
+  }
   if (tid == 0) {
     for (int i = 0; i < C::NSLOT; ++i) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(bFull + i)), "r"(NCW));
@@ -435,6 +508,8 @@ fbf_tc_kernel(const __grid_constant__ DeviceParams p, const Work w, const Scratc
     }
     for (int i = 0; i < 4; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(bXa + i)));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(bFd)), "r"(NCW));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(bRa)), "r"(NCW));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(bRb)), "r"(NCW));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(bDrain)));
     *sAbort = 0;
   }
@@ -480,8 +555,8 @@ fbf_tc_kernel(const __grid_constant__ DeviceParams p, const Work w, const Scratc
 
   if (warp == NCW) {
     // ===================== MMA issuer ======================================================
-    // Issue order per pair: x(a), x(b), y(a), y(b).  Each barrier it waits on completes while
-    // the tensor pipe still holds the previously issued pass, so the pipe does not drain.
+    // Issue order per pair: the x passes of both images chunk by chunk, then y(a), y(b).  The
+    // y pass of an image waits for its D1 to be rounded by the compute warps.
     {
       // every lane waits; a wait counts as given up when any lane gave up
       auto wait_all = [&](uint64_t* bar, uint32_t par) { return __all_sync(0xffffffffu, mbar_wait(bar, par, sAbort)); };
@@ -490,8 +565,9 @@ fbf_tc_kernel(const __grid_constant__ DeviceParams p, const Work w, const Scratc
       const uint32_t idY = instr_desc(2u, TILE_X, TILE_Y);
       const uint64_t dGy = op_desc(smem_u32(sGy), 32 * C::KY);
       const uint64_t dBh = op_desc(smem_u32(sBh), 16 * C::CW);
+      const uint64_t dGl = op_desc(smem_u32(sGl), 16 * C::KX);
       uint32_t P = 0;
-      int slot0 = 0, ring0 = 0;        // ring slot and use count of the pair's first chunk
+      int slot0 = 0, ring0 = 0;        // ring slot and use count of the next chunk
       bool ab = false;
       int img = img0;
       long long u = u0;
@@ -501,31 +577,36 @@ fbf_tc_kernel(const __grid_constant__ DeviceParams p, const Work w, const Scratc
         const int ke = (img == img_end && t == u_end / K) ? (int)(u_end - t * K) : K;
         const int np = frag_pairs(kb, ke);
         for (int j = 0; j < np; ++j, ++P) {
+          // D1 is free once the previous pair's y passes have completed
+          if (P > 0 && (!wait_all(bYa, (P - 1) & 1) || !wait_all(bYb, (P - 1) & 1))) { ab = true; break; }
+          // x passes of both images, chunk by chunk (each chunk slot is released as soon as
+          // both images have consumed it)
+          for (int c = 0; c < C::NC; ++c) {
+            if (!wait_all(bFull + slot0, ring0 & 1)) { ab = true; break; }
+            tc_fence_after();
 #pragma unroll
-          for (int s = 0; s < 2; ++s) {
-            // D1[s] is free once y(s) of the previous pair has completed
-            if (P > 0 && !wait_all(s ? bYb : bYa, (P - 1) & 1)) { ab = true; break; }
-            int sl = slot0, rg = ring0;
-            for (int c = 0; c < C::NC; ++c) {
-              if (s == 0 && !wait_all(bFull + sl, rg & 1)) { ab = true; break; }
-              tc_fence_after();
+            for (int s = 0; s < 2; ++s) {
 #pragma unroll
               for (int kk = 0; kk < C::CK; ++kk) {
                 const int ks = c * C::CK + kk;
-                mma_ts_f16(tmem + C::D1C + s * C::D1S, tmem + C::GXC + 8 * ks,
-                           dBh + (uint64_t)(((2 * sl + s) * C::CB + kk * 256) >> 4), idX, ks > 0);
+                const uint64_t bhi = dBh + (uint64_t)((slot0 * C::SLOTB + s * C::CB + kk * 256) >> 4);
+                mma_ts_f16(tmem + C::D1C + s * C::D1S, tmem + C::GXC + 8 * ks, bhi, idX, ks > 0 ? 1u : 0u);
+                if (NPART == 2) {
+                  mma_ts_f16(tmem + C::D1C + s * C::D1S, tmem + C::GXC + 8 * ks,
+                             bhi + (uint64_t)((2 * C::CB) >> 4), idX, 1u);
+                  mma_ss_el(tmem + C::D1C + s * C::D1S, dGl + (uint64_t)(16 * ks), bhi, idX, 1u);
+                }
               }
-              if (s == 1) mma_commit_el(bEmpty + sl);   // both images of the chunk consumed
-              if (++sl == C::NSLOT) { sl = 0; ++rg; }
+              if (c == C::NC - 1) mma_commit_el(s ? bXb : bXa);
             }
-            if (ab) break;
-            mma_commit_el(s ? bXb : bXa);
-            if (s == 1) { slot0 = sl; ring0 = rg; }
+            mma_commit_el(bEmpty + slot0);
+            if (++slot0 == C::NSLOT) { slot0 = 0; ++ring0; }
           }
           if (ab) break;
 #pragma unroll
           for (int s = 0; s < 2; ++s) {
-            if (!wait_all(s ? bXb : bXa, P & 1)) { ab = true; break; }
+            // the compute warps round D1 to nearest TF32 once the x pass is complete
+            if (!wait_all(s ? bRb : bRa, P & 1)) { ab = true; break; }
             // D2 is free once the previous pair has been folded
             if (s == 0 && P > 0 && !wait_all(bFd, (P - 1) & 1)) { ab = true; break; }
             tc_fence_after();
@@ -560,7 +641,39 @@ fbf_tc_kernel(const __grid_constant__ DeviceParams p, const Work w, const Scratc
     long long u = u0;
     float nm[PX], dn[PX];
 
-    auto wtab = [&](int k, int kind) { return sTab + (k & 1) * C::TABW + 512 + (kind == 2 ? 256 : 0); };
+    // D1 of image s rounded to nearest TF32 in place: the y pass reads its A operand from
+    // tensor memory as TF32, which drops the low mantissa bits (truncation); rounding first
+    // keeps the error unbiased.  Warp (q, rg) takes the 8-column chunks rg, rg + 4, ...
+    auto round_d1 = [&](uint32_t Pr, int s) {
+      if (!mbar_wait(s ? bXb : bXa, Pr & 1, sAbort)) { ab = true; *sAbort = 1; }
+      tc_fence_after();
+      const uint32_t d1 = tmem + ((uint32_t)(32 * q) << 16) + C::D1C + s * C::D1S;
+      constexpr int NCH = C::KY / 8;
+#pragma unroll
+      for (int c0 = 0; c0 < NCH; c0 += 8) {   // two chunks per warp at a time
+        uint32_t v[2][8];
+#pragma unroll
+        for (int jj = 0; jj < 2; ++jj) {
+          const int c = c0 + rg + 4 * jj;
+          if (c < NCH) tmem_ld8(d1 + 8 * c, v[jj]);
+        }
+        tmem_wait_ld();
+#pragma unroll
+        for (int jj = 0; jj < 2; ++jj) {
+          const int c = c0 + rg + 4 * jj;
+          if (c < NCH) {
+#pragma unroll
+            for (int e = 0; e < 8; ++e) v[jj][e] = to_tf32(__uint_as_float(v[jj][e]));
+            tmem_st8(d1 + 8 * c, v[jj]);
+          }
+        }
+      }
+      tmem_wait_st();
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(s ? bRb : bRa);
+    };
+    auto wtab = [&](int k, int kind) { return sTab + (k & 1) * C::TABW + 2 * C::GENW + (kind == 2 ? 256 : 0); };
     // own pixels' weights for rows h .. h + 7 (table path: the pair's weight table)
     auto weights8 = [&](int h, int k, int kind, bool tile_int, int tx0, int ty0, const uint32_t* wt, float (&wv)[8]) {
       const unsigned char* own = sFh + (oy0 + RAD + h) * C::FHS + ox + RAD;
@@ -630,14 +743,14 @@ fbf_tc_kernel(const __grid_constant__ DeviceParams p, const Work w, const Scratc
         pair_of(kb, j, &k, &kind);
         // the term's tables are built at its first pair; slot k & 1 is free by then (its
         // previous term was last read by a fold before the previous pair's barrier)
-        uint32_t* tslot = sTab + (k & 1) * C::TABW + (kind == 2 ? 256 : 0);
-        if (tile_int && kind != 2) build_term_table<T>(p, k, sTab + (k & 1) * C::TABW, tid);
+        uint32_t* tslot = sTab + (k & 1) * C::TABW + (kind == 2 ? C::GENW : 0);
+        if (tile_int && kind != 2) build_term_table<T, NPART>(p, k, sTab + (k & 1) * C::TABW, tid);
         ab = sync_compute_or(ab || *sAbort);   // also publishes the table
         if (ab) break;
         // a ring slot is free once the x pass has consumed the chunk it held NSLOT chunks ago
         for (int c = 0; c < C::NC; ++c) {
           if (ring > 0 && !mbar_wait(bEmpty + slot, (ring - 1) & 1, sAbort)) { ab = true; *sAbort = 1; }
-          gen_chunk<RAD, T>(sBh + 2 * slot * C::CB, c, sFh, tslot, tile_int, interior, tx0, ty0, H, W, w.in,
+          gen_chunk<RAD, T>(sBh + slot * C::SLOTB, c, sFh, tslot, tile_int, interior, tx0, ty0, H, W, w.in,
                             pitch, k, kind, p, tid);
           proxy_fence();
           __syncwarp();
@@ -645,6 +758,8 @@ fbf_tc_kernel(const __grid_constant__ DeviceParams p, const Work w, const Scratc
           if (++slot == C::NSLOT) { slot = 0; ++ring; }
         }
         if (j > 0) fold(P - 1, kprev, kindprev, tile_int, tx0, ty0, wtab(kprev, kindprev));
+        round_d1(P, 0);
+        round_d1(P, 1);
         kprev = k;
         kindprev = kind;
       }
@@ -728,7 +843,7 @@ fbf_tc_kernel(const __grid_constant__ DeviceParams p, const Work w, const Scratc
 template <int RAD, typename T>
 int launch_rad(const DeviceParams& dp, const float* in, float* out, int H, int W, size_t pitch,
                cudaStream_t st) {
-  using C = TcCfg<RAD>;
+  using C = TcCfg<RAD, Parts<T>::value>;
   static int occ[64] = {0};
   static int sms[64] = {0};
   int dev = 0;

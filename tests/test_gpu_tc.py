@@ -1,11 +1,12 @@
 """Tensor-core forms (FBF_FP16_TC, FBF_BF16_TC) against the FP64 oracle, through the C ABI.
 
-Both Gaussian passes run on the tensor cores with FP16 or BF16 operands (the convolved
-images, the banded Toeplitz tap matrix and the x-pass result are rounded to the operand
-type) and FP32 accumulation.  Tolerances: the FP16 form must meet the 0.5 gray-level bound
-stated for the low-precision stack; measured maxima are ~0.13.  The BF16 form
-(7-bit mantissa) measures up to ~0.8 at sigma = 10 and is checked against 1.5 only, to catch
-gross errors; it does not meet the 0.5 bound.
+Both Gaussian passes run on the tensor cores with FP32 accumulation.  The x pass takes the
+convolved images and the banded Toeplitz taps as FP16 (FBF_FP16_TC) or as compensated BF16
+pairs hi + lo (FBF_BF16_TC); its result is rounded to nearest TF32 for the y pass, whose taps
+are TF32.  Tolerance: the 0.5 gray-level bound stated for the 16-bit stack.  The FP16 form
+meets it on these images (max ~0.13) but not everywhere: where the bilateral denominator is
+small (a pixel unlike its whole window, e.g. at theta 10, sigma 10, noise 15) FP16 operand
+rounding reaches ~1.8, which the compensated BF16 form brings to ~0.6 (test below).
 """
 import numpy as np
 import pytest
@@ -16,7 +17,7 @@ from paper_1811_02168_gb300.synth import voronoi_image
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
-TOL = {"fp16": 0.5, "bf16": 1.5}
+TOL = {"fp16": 0.5, "bf16": 0.5}
 
 
 @pytest.fixture(scope="module")
@@ -74,3 +75,33 @@ def test_tc_radius_limit(B):
     with pytest.raises(B.FbfError) as ei:
         B.Plan(30.0, 255, 10.5, K=4, precision=B.FBF_FP16_TC)   # r = 32 > 30
     assert ei.value.code == B.FBF_EUNSUPPORTED
+
+
+def test_bf16_compensated_on_small_denominators(B):
+    """A 256 x 256 window of the 4096 x 4096 theta-10 workload image (noise 15) that holds
+    pixels whose bilateral denominator is near its minimum (the centre tap alone).  There
+    the remaining error of the compensated form is the TF32 rounding of the x-pass result
+    in the y pass (a CPU model of the arithmetic gives 0.59 here, 0.01 with that value split
+    too); FP16 operands give 1.78.  Checked against that measured limit, not the 0.5 bound."""
+    from paper_1811_02168_gb300.synth import workload_large
+    img = workload_large().image()[:256, 2816:3072].copy()
+    op = ofit.make_plan(10.0, 255, K=16)
+    ref = ofl.fourier_bf(img.astype(np.float64), 10.0, op.c, op.T)
+    errs = {}
+    for form, prec in (("fp16", B.FBF_FP16_TC), ("bf16", B.FBF_BF16_TC)):
+        plan = B.Plan(10.0, 255, 10.0, K=16, precision=prec)
+        errs[form] = float(np.abs(_run(B, plan, img) - ref).max())
+    assert errs["bf16"] <= 0.75, errs
+    assert errs["bf16"] < 0.5 * errs["fp16"], errs
+    assert B.fbf_device_errors() == 0
+
+
+def test_bf16_non_integer_input(B):
+    rng = np.random.default_rng(6)
+    img = (voronoi_image(130, 150, 12, 30.0, 10.0, seed=37) * 0.9 +
+           rng.uniform(0.0, 0.999, (130, 150))).astype(np.float32)
+    plan = B.Plan(15.0, 255, 5.0, K=8, precision=B.FBF_BF16_TC)
+    op = ofit.make_plan(15.0, 255, K=8)
+    ref = ofl.fourier_bf(img.astype(np.float64), 5.0, op.c, op.T)
+    assert float(np.abs(_run(B, plan, img) - ref).max()) <= TOL["bf16"]
+    assert B.fbf_device_errors() == 0
