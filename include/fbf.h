@@ -47,9 +47,17 @@ extern "C" {
 
 /* ---- precision forms (fbf_plan's `precision`) --------------------------------- */
 #define FBF_FP32       0   /* FP32 channel stack and FP32 FIR on the CUDA cores       */
-#define FBF_FP16_TC    1   /* FP16 channel stack, both Gaussian passes on the tensor
-                              cores (tcgen05, banded Toeplitz operand), FP32 accumulate */
-#define FBF_BF16_TC    2   /* as FBF_FP16_TC with BF16 operands                      */
+/* Tensor-core forms: both Gaussian passes of Section II run as banded Toeplitz
+   contractions on the tensor cores (tcgen05) with FP32 accumulation.  The x pass takes
+   the channel stack and its taps as 16-bit operands; its result is rounded to nearest
+   TF32 and contracted with TF32 taps in the y pass.  Recombination and divide are FP32.
+   Errors against the FP64 oracle grow where the bilateral denominator is small (a pixel
+   unlike its whole window): see the precision section of the design notes.            */
+#define FBF_FP16_TC    1   /* FP16 stack and taps (fastest; ~0.13 max error on typical
+                              8-bit images, up to ~1.8 at small denominators)          */
+#define FBF_BF16_TC    2   /* compensated BF16 stack and taps: every value is a hi + lo
+                              BF16 pair (three x-pass products); ~0.08 typical, ~0.6 at
+                              small denominators                                       */
 
 /* ---- flags (fbf_plan's `flags`) ----------------------------------------------- */
 #define FBF_FLAG_FIXED_PERIOD 1  /* T = R (fixed period, the FBF model the paper
