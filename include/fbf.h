@@ -217,6 +217,22 @@ int fbf_batch_pending(fbf_batch_t batch, int* n);
 int fbf_batch_destroy(fbf_batch_t batch);
 
 /* fbf_last_error -- message for the last failing call on this thread ("" if none). */
+/*
+ * fbf_brute_filter -- eq. (1) evaluated directly with the Gaussian range kernel of eq. (2)
+ * (no cosine series): for every pixel, weights g(j_x) g(j_y) exp(-(f(i-j) - f(i))^2 /
+ * (2 sigma^2)) over the (2r+1)^2 window, r = ceil(3 theta), g(x) = exp(-x^2/(2 theta^2));
+ * pixels outside the image are absent from both sums.  The accuracy reference against
+ * which the paper measures PSNR (Section III); cost 2(6 theta + 1)^2 per pixel (Section I).
+ *
+ * d_in, d_out: device pointers to H x W float32 images, row stride pitch_elems elements
+ * (>= W), not overlapping.  theta, sigma > 0, R >= 1 (the intensity range [0, R]; integer
+ * tiles with values <= min(R, 1023) use a table of the range kernel).  r > FBF_MAX_RADIUS
+ * returns FBF_EUNSUPPORTED.  Asynchronous on cuda_stream (NULL = legacy default stream);
+ * FP32 arithmetic.  No plan and no scratch memory.
+ */
+int fbf_brute_filter(const float* d_in, float* d_out, int H, int W, size_t pitch_elems,
+                     double theta, double sigma, int R, void* cuda_stream);
+
 const char* fbf_last_error(void);
 
 /* fbf_device_errors -- synchronise nothing; read (and with clear != 0 reset) the device

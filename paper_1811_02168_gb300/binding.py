@@ -55,6 +55,9 @@ SIGNATURES = {
                                   ctypes.c_int, ctypes.c_size_t, ctypes.c_void_p]),
     "fbf_filter_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                           ctypes.c_int, ctypes.c_size_t, ctypes.c_void_p]),
+    "fbf_brute_filter": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_size_t, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                        ctypes.c_void_p]),
     "fbf_batch_create": (ctypes.c_int, [_c_void_pp, ctypes.c_int, ctypes.c_int]),
     "fbf_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                   ctypes.c_int, ctypes.c_int, ctypes.c_size_t,
@@ -197,6 +200,13 @@ def fbf_device_errors(clear: bool = False) -> int:
     f = ctypes.c_int()
     _check(lib().fbf_device_errors(ctypes.byref(f), 1 if clear else 0), "fbf_device_errors")
     return f.value
+
+
+def fbf_brute_filter(d_in: int, d_out: int, H: int, W: int, pitch_elems: int, theta: float, sigma: float,
+                     R: int = 255, stream: int = 0) -> None:
+    """Eq. (1) with the Gaussian range kernel, evaluated directly on the device (device
+    pointers, asynchronous on `stream`)."""
+    _check(lib().fbf_brute_filter(d_in, d_out, H, W, pitch_elems, theta, sigma, R, stream), "fbf_brute_filter")
 
 
 def fbf_last_error() -> str:

@@ -195,3 +195,18 @@ def test_batch_host_side_queue_and_bounded_wait():
         B.fbf_batch_destroy(b)
     with pytest.raises(B.FbfError):
         B.fbf_batch_create(0, 0)
+
+
+def test_brute_filter_argument_errors():
+    from paper_1811_02168_gb300 import binding as B
+    L = B.lib()
+    x = ctypes.c_void_p(16)
+    y = ctypes.c_void_p(1 << 20)
+    assert L.fbf_brute_filter(None, y, 4, 4, 4, 2.0, 30.0, 255, None) == B.FBF_EINVAL
+    assert L.fbf_brute_filter(x, y, 0, 4, 4, 2.0, 30.0, 255, None) == B.FBF_EINVAL
+    assert L.fbf_brute_filter(x, y, 4, 4, 3, 2.0, 30.0, 255, None) == B.FBF_EINVAL
+    assert L.fbf_brute_filter(x, y, 4, 4, 4, 0.0, 30.0, 255, None) == B.FBF_EINVAL
+    assert L.fbf_brute_filter(x, y, 4, 4, 4, 2.0, -1.0, 255, None) == B.FBF_EINVAL
+    assert L.fbf_brute_filter(x, y, 4, 4, 4, 2.0, 30.0, 0, None) == B.FBF_EINVAL
+    assert L.fbf_brute_filter(x, x, 4, 4, 4, 2.0, 30.0, 255, None) == B.FBF_EINVAL   # overlap
+    assert L.fbf_brute_filter(x, y, 4, 4, 4, 17.0, 30.0, 255, None) == B.FBF_EUNSUPPORTED   # r = 51
