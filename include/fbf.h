@@ -233,6 +233,34 @@ int fbf_batch_destroy(fbf_batch_t batch);
 int fbf_brute_filter(const float* d_in, float* d_out, int H, int W, size_t pitch_elems,
                      double theta, double sigma, int R, void* cuda_stream);
 
+/* ---- lookup table of K* and T* (Section II, after Algorithm 1; Fig. 2) ------------
+ * The paper runs Algorithm 1 offline on a grid of (sigma, eps), stores K* and T*, and at run
+ * time reads them (bilinear interpolation in sigma and log(1/eps) off the grid) and solves
+ * only the least squares of eq. (5) for the coefficients.  Gaussian range kernel of eq. (2)
+ * on the intensity range [0, R].  Host only; a table owns host memory only. */
+typedef struct fbf_lut_s* fbf_lut_t;
+
+/* Run Algorithm 1 at every grid point.  sigmas: n_sigma >= 2 values, strictly increasing,
+ * > 0; eps: n_eps >= 2 values in (0, 1), strictly decreasing (so log(1/eps) increases).
+ * Errors: FBF_EINVAL for bad grids, or the fitter's code when a point cannot be fitted. */
+int fbf_lut_build(fbf_lut_t* out, int R, const double* sigmas, int n_sigma, const double* eps, int n_eps);
+
+/* K* and T* stored at grid point (i_sigma, j_eps). */
+int fbf_lut_entry(fbf_lut_t lut, int i_sigma, int j_eps, int* K, int* T);
+
+/* Bilinear interpolation of K* and T* in (sigma, log(1/eps)), each rounded to the nearest
+ * integer.  (sigma, eps) outside the grid: FBF_EUNSUPPORTED. */
+int fbf_lut_lookup(fbf_lut_t lut, double sigma, double eps, int* K, int* T);
+
+/* A plan (as fbf_plan) whose K and T come from fbf_lut_lookup; only c is fitted (eq. 5). */
+int fbf_plan_from_lut(fbf_plan_t* out, fbf_lut_t lut, double sigma, double eps, double theta, int precision);
+
+/* Text file: "fbf-lut 1", R n_sigma n_eps, the sigmas, the eps values, then K T per grid
+ * point (sigma-major).  fbf_lut_load checks the format (FBF_EINVAL when malformed). */
+int fbf_lut_save(fbf_lut_t lut, const char* path);
+int fbf_lut_load(fbf_lut_t* out, const char* path);
+int fbf_lut_destroy(fbf_lut_t lut);
+
 const char* fbf_last_error(void);
 
 /* fbf_device_errors -- synchronise nothing; read (and with clear != 0 reset) the device

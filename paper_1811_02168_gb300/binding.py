@@ -58,6 +58,15 @@ SIGNATURES = {
     "fbf_brute_filter": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                         ctypes.c_size_t, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                         ctypes.c_void_p]),
+    "fbf_lut_build": (ctypes.c_int, [_c_void_pp, ctypes.c_int, _c_double_p, ctypes.c_int, _c_double_p,
+                                     ctypes.c_int]),
+    "fbf_lut_entry": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, _c_int_p, _c_int_p]),
+    "fbf_lut_lookup": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, _c_int_p, _c_int_p]),
+    "fbf_plan_from_lut": (ctypes.c_int, [_c_void_pp, ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
+                                         ctypes.c_double, ctypes.c_int]),
+    "fbf_lut_save": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p]),
+    "fbf_lut_load": (ctypes.c_int, [_c_void_pp, ctypes.c_char_p]),
+    "fbf_lut_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "fbf_batch_create": (ctypes.c_int, [_c_void_pp, ctypes.c_int, ctypes.c_int]),
     "fbf_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                   ctypes.c_int, ctypes.c_int, ctypes.c_size_t,
@@ -209,6 +218,51 @@ def fbf_brute_filter(d_in: int, d_out: int, H: int, W: int, pitch_elems: int, th
     _check(lib().fbf_brute_filter(d_in, d_out, H, W, pitch_elems, theta, sigma, R, stream), "fbf_brute_filter")
 
 
+class Lut:
+    """Owns an ``fbf_lut_t``: Algorithm 1 on a (sigma, eps) grid, bilinear lookup off the grid."""
+
+    def __init__(self, R: int = 255, sigmas=None, eps=None, path: str | None = None):
+        h = ctypes.c_void_p()
+        if path is not None:
+            _check(lib().fbf_lut_load(ctypes.byref(h), os.fsencode(path)), "fbf_lut_load")
+        else:
+            s = (ctypes.c_double * len(sigmas))(*sigmas)
+            e = (ctypes.c_double * len(eps))(*eps)
+            _check(lib().fbf_lut_build(ctypes.byref(h), R, s, len(sigmas), e, len(eps)), "fbf_lut_build")
+        self.handle = h.value
+        self.R = R
+
+    def entry(self, i: int, j: int):
+        K, T = ctypes.c_int(), ctypes.c_int()
+        _check(lib().fbf_lut_entry(self.handle, i, j, ctypes.byref(K), ctypes.byref(T)), "fbf_lut_entry")
+        return K.value, T.value
+
+    def lookup(self, sigma: float, eps: float):
+        K, T = ctypes.c_int(), ctypes.c_int()
+        _check(lib().fbf_lut_lookup(self.handle, sigma, eps, ctypes.byref(K), ctypes.byref(T)), "fbf_lut_lookup")
+        return K.value, T.value
+
+    def plan(self, sigma: float, eps: float, theta: float, precision: int = FBF_FP32) -> "Plan":
+        h = ctypes.c_void_p()
+        _check(lib().fbf_plan_from_lut(ctypes.byref(h), self.handle, sigma, eps, theta, precision),
+               "fbf_plan_from_lut")
+        return Plan._adopt(h.value, sigma, self.R, theta, precision)
+
+    def save(self, path: str) -> None:
+        _check(lib().fbf_lut_save(self.handle, os.fsencode(path)), "fbf_lut_save")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().fbf_lut_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def fbf_last_error() -> str:
     return lib().fbf_last_error().decode()
 
@@ -238,6 +292,15 @@ class Plan:
         self.sigma, self.R, self.theta, self.precision, self.flags = sigma, R, theta, precision, flags
         self.K, self.T, self.c, self.E, self.delta_max = fbf_plan_info(self.handle)
         self.radius = fbf_plan_radius(self.handle)
+
+    @classmethod
+    def _adopt(cls, handle: int, sigma, R: int, theta: float, precision: int) -> "Plan":
+        p = cls.__new__(cls)
+        p.handle = handle
+        p.sigma, p.R, p.theta, p.precision, p.flags = sigma, R, theta, precision, 0
+        p.K, p.T, p.c, p.E, p.delta_max = fbf_plan_info(handle)
+        p.radius = fbf_plan_radius(handle)
+        return p
 
     def close(self):
         if getattr(self, "handle", None):

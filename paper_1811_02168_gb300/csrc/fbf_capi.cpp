@@ -36,8 +36,15 @@ bool precision_known(int precision) {
   return precision == FBF_FP32 || precision == FBF_FP16_TC || precision == FBF_BF16_TC;
 }
 
+}  // namespace
+
+namespace fbf {
+
+// A plan from kernel samples b(-R..R).  T_given > 0 fixes the period parameter (with K >= 1:
+// only the least squares of eq. (5) for c runs, as with a lookup table); otherwise T follows
+// FBF_FLAG_FIXED_PERIOD (T = R) or the optimisation of eq. (6) / Algorithm 1.
 int build_plan(fbf_plan_t* out, const double* b, int R, double theta, int K, double eps,
-               int precision, int flags, double sigma) {
+               int precision, int flags, double sigma, int T_given) {
   if (!out) return fbf::set_error(FBF_EINVAL, "fbf_plan: out is NULL");
   *out = nullptr;
   if (R < 1) return fbf::set_error(FBF_EINVAL, "fbf_plan: R must be >= 1");
@@ -64,7 +71,7 @@ int build_plan(fbf_plan_t* out, const double* b, int R, double theta, int K, dou
   p.precision = precision;
   p.flags = flags;
   std::string msg;
-  int T_fixed = (flags & FBF_FLAG_FIXED_PERIOD) ? R : 0;
+  int T_fixed = (flags & FBF_FLAG_FIXED_PERIOD) ? R : (T_given > 0 ? T_given : 0);
   int rc = fbf::fit_range_kernel(b, R, K, eps, T_fixed, &p.fit, &msg);
   if (rc != FBF_OK) { delete h; return fbf::set_error(rc, "fbf_plan: " + msg); }
   if (p.fit.K > FBF_MAX_K) { delete h; return fbf::set_error(FBF_EUNSUPPORTED, "fbf_plan: fitted K exceeds FBF_MAX_K"); }
@@ -99,7 +106,9 @@ int build_plan(fbf_plan_t* out, const double* b, int R, double theta, int K, dou
   return FBF_OK;
 }
 
-}  // namespace
+}  // namespace fbf
+
+using fbf::build_plan;
 
 extern "C" {
 
@@ -117,7 +126,7 @@ int fbf_plan(fbf_plan_t* out, double sigma, int R, double theta, int K, double e
   double* b = new (std::nothrow) double[2 * R + 1];
   if (!b) return fbf::set_error(FBF_ENOMEM, "fbf_plan: out of host memory");
   for (int t = -R; t <= R; ++t) b[t + R] = std::exp(-(double)t * t / (2.0 * sigma * sigma));
-  int rc = build_plan(out, b, R, theta, K, eps, precision, flags, sigma);
+  int rc = build_plan(out, b, R, theta, K, eps, precision, flags, sigma, 0);
   delete[] b;
   return rc;
 }
@@ -132,7 +141,7 @@ int fbf_plan_from_samples(fbf_plan_t* out, const double* b, int R, double theta,
     if (out) *out = nullptr;
     return fbf::set_error(FBF_EINVAL, "fbf_plan_from_samples: R out of range");
   }
-  return build_plan(out, b, R, theta, K, eps, precision, flags, NAN);
+  return build_plan(out, b, R, theta, K, eps, precision, flags, NAN, 0);
 }
 
 int fbf_plan_info(fbf_plan_t plan, int* K, int* T, double* c, double* E, double* delta_max) {

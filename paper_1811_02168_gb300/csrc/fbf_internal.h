@@ -28,6 +28,10 @@ struct FitResult {
 int fit_range_kernel(const double* b, int R, int K, double eps, int T_fixed,
                      FitResult* out, std::string* msg);
 
+// Plan from kernel samples (fbf_capi.cpp); T_given > 0 fixes the period parameter.
+int build_plan(struct fbf_plan_s** out, const double* b, int R, double theta, int K, double eps,
+               int precision, int flags, double sigma, int T_given);
+
 // E(K,T) for K = 1..Kc at one T (folded Householder QR); used by tests via the C ABI.
 void kernel_error_curve(const double* b, int R, int T, int Kc, double* E_out);
 
