@@ -163,8 +163,9 @@ typedef uint64_t fbf_ticket_t;
 
 /*
  * fbf_batch_create -- a batch context.  Images are queued with fbf_submit and filtered
- * together by fbf_launch: per radius class (the kernel instantiation serving their
- * r = ceil(3 theta)) one persistent stream-K launch runs over a device work-list of all
+ * together by fbf_launch: per precision form and radius class (the kernel instantiation
+ * serving their r = ceil(3 theta)) one persistent stream-K launch runs over a device
+ * work-list of all
  * (image, tile, cosine term) units, so small and large images share the GPU evenly.  Not
  * in the paper (Section III filters one image at a time); the arithmetic per image is
  * exactly fbf_filter's.  max_images (>= 1) bounds one launch; flags: FBF_BATCH_AUTOTUNE,
@@ -179,11 +180,11 @@ int fbf_batch_create(fbf_batch_t* out, int max_images, int flags);
 
 /*
  * fbf_submit -- queue one image (host-side only; nothing runs until fbf_launch).  Arguments
- * as fbf_filter; FBF_FP32 plans only.  The plan must stay alive until the fbf_launch or
+ * as fbf_filter, any precision form.  The plan must stay alive until the fbf_launch or
  * fbf_batch_capture call that takes the image returns (its parameters are copied then).
  * *ticket (may be NULL) identifies the launch the image will belong to.
  * Errors: FBF_EINVAL (bad arguments), FBF_EBUSY (max_images already queued),
- * FBF_EUNSUPPORTED (other precision forms, radius beyond FBF_MAX_RADIUS).
+ * FBF_EUNSUPPORTED (radius beyond the form's limit: FBF_MAX_RADIUS, FBF_MAX_RADIUS_TC).
  */
 int fbf_submit(fbf_batch_t batch, fbf_plan_t plan, const float* d_in, float* d_out, int H, int W,
                size_t pitch_elems, fbf_ticket_t* ticket);

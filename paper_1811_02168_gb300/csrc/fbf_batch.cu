@@ -44,6 +44,7 @@ struct ClassLaunch {
   int (*partial_bytes)(int dev, size_t* out);
   int TY;
   const char* name;
+  int TX = fp32::TX;   // tile width of the kernel's schedule
 };
 
 template <int RAD, int TY, int NT, int NY>
@@ -102,7 +103,21 @@ constexpr ClassLaunch cfg_entry(const char* name) {
 struct RadClass {
   int rad;
   std::vector<ClassLaunch> cands;   // first = default
+  int precision = FBF_FP32;
 };
+
+// tensor-core forms: one configuration per (radius class, precision), 128 x 64 tiles
+template <int RAD, int PREC>
+int tc_launch(const DeviceParams* dparams, const Work* dwork, int n, long long wtot, float* partial, int* counter,
+              cudaStream_t st, int dev) {
+  return launch_tc_batch(RAD, PREC, dparams, dwork, n, wtot, partial, counter, st, dev);
+}
+template <int RAD, int PREC>
+ClassLaunch tc_entry(const char* name) {
+  ClassLaunch c{&tc_launch<RAD, PREC>, &tc_batch_partial_bytes, 64, name};
+  c.TX = 128;
+  return c;
+}
 
 const std::vector<RadClass>& classes() {
   static const std::vector<RadClass> cls = {
@@ -113,14 +128,21 @@ const std::vector<RadClass>& classes() {
       {24, {cfg_entry<24, 128, 256, 16>("r24_ty128_nt256")}},
       {30, {cfg_entry<30, 128, 256, 16>("r30_ty128_nt256"), cfg_entry<30, 96, 256, 12>("r30_ty96_nt256")}},
       {48, {cfg_entry<48, 64, 128, 16>("r48_ty64_nt128")}},
+      {6, {tc_entry<6, FBF_FP16_TC>("tc_fp16_r6")}, FBF_FP16_TC},
+      {15, {tc_entry<15, FBF_FP16_TC>("tc_fp16_r15")}, FBF_FP16_TC},
+      {30, {tc_entry<30, FBF_FP16_TC>("tc_fp16_r30")}, FBF_FP16_TC},
+      {6, {tc_entry<6, FBF_BF16_TC>("tc_bf16_r6")}, FBF_BF16_TC},
+      {15, {tc_entry<15, FBF_BF16_TC>("tc_bf16_r15")}, FBF_BF16_TC},
+      {30, {tc_entry<30, FBF_BF16_TC>("tc_bf16_r30")}, FBF_BF16_TC},
   };
   return cls;
 }
 
-int class_of(int r) {
+// the narrowest class of the plan's precision form that holds radius r
+int class_of(int r, int precision) {
   const auto& cls = classes();
   for (size_t i = 0; i < cls.size(); ++i)
-    if (r <= cls[i].rad) return (int)i;
+    if (cls[i].precision == precision && r <= cls[i].rad) return (int)i;
   return -1;
 }
 
@@ -252,7 +274,7 @@ struct ClassPlan {
 int build_lists(Batch* b, std::vector<ClassPlan>* out, size_t* bytes) {
   std::map<int, ClassPlan> by;
   for (const Pending& pd : b->pending) {
-    const int cls = class_of(pd.plan->r);
+    const int cls = class_of(pd.plan->r, pd.plan->precision);
     if (cls < 0) return set_error(FBF_EUNSUPPORTED, "fbf_launch: radius too large");
     ClassPlan& cp = by[cls];
     cp.cls = cls;
@@ -294,9 +316,10 @@ int build_lists(Batch* b, std::vector<ClassPlan>* out, size_t* bytes) {
 // tile geometry of a class plan for candidate `cand`
 void layout(ClassPlan& cp, int cand) {
   const int TY = classes()[cp.cls].cands[cand].TY;
+  const int TXc = classes()[cp.cls].cands[cand].TX;
   long long wst = 0, tiles = 0;
   for (Work& w : cp.works) {
-    w.tiles_x = (w.W + TX - 1) / TX;
+    w.tiles_x = (w.W + TXc - 1) / TXc;
     w.tiles_y = (w.H + TY - 1) / TY;
     w.tiles = (long long)w.tiles_x * w.tiles_y;
     w.wstart = wst;
@@ -530,8 +553,7 @@ int fbf_submit(fbf_batch_t batch, fbf_plan_t plan, const float* d_in, float* d_o
   if (H < 1 || W < 1) return fbf::set_error(FBF_EINVAL, "fbf_submit: H and W must be >= 1");
   if (pitch_elems < (size_t)W) return fbf::set_error(FBF_EINVAL, "fbf_submit: pitch < W");
   const fbf::Plan* p = fbf::plan_of(plan);
-  if (p->precision != FBF_FP32) return fbf::set_error(FBF_EUNSUPPORTED, "fbf_submit: only the FBF_FP32 form");
-  if (fbf::class_of(p->r) < 0) return fbf::set_error(FBF_EUNSUPPORTED, "fbf_submit: radius too large");
+  if (fbf::class_of(p->r, p->precision) < 0) return fbf::set_error(FBF_EUNSUPPORTED, "fbf_submit: radius too large for the plan's form");
   const size_t span = ((size_t)(H - 1) * pitch_elems + (size_t)W) * sizeof(float);
   const char* a = (const char*)d_in;
   const char* o = (const char*)d_out;

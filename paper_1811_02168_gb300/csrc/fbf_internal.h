@@ -85,6 +85,12 @@ int launch_tc(const DeviceParams& dp, const float* in, float* out, int H, int W,
               void* stream, int precision);
 // Device error word of the tensor-core kernels (bit 0: a bounded wait gave up).
 int device_errors(int* flags, int clear);
+
+// batched tensor-core launch of one radius class (6, 15 or 30) from a device work-list
+namespace fp32 { struct Work; }
+int launch_tc_batch(int rad, int precision, const DeviceParams* dparams, const fp32::Work* dwork, int n,
+                    long long wtot, float* partial, int* counter, void* stream, int dev);
+int tc_batch_partial_bytes(int dev, size_t* out);
 // Same kernel, scratch from a fixed device array instead of the per-stream workspace.
 int launch_fp32_noalloc(const DeviceParams& dp, const float* in, float* out, int H, int W,
                         size_t pitch, void* stream);

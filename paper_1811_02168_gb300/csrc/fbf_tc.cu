@@ -47,6 +47,7 @@ namespace tc {
 using fp32::Work;
 using fp32::Scratch;
 using fp32::SingleSrc;
+using fp32::ListSrc;
 using fp32::ceil_div_ll;
 using fp32::term_start;
 using fp32::locate;
@@ -446,9 +447,60 @@ __device__ __forceinline__ void gen_chunk(unsigned char* dst, int c, const unsig
   }
 }
 
+// Taps of an image's radius class into the operand layouts: Gy (TF32, shared memory), Gx_lo
+// (compensated form, shared memory) by all compute threads; Gx (tensor memory, lanes
+// x' = 32 warp + lane, two K elements per column) by compute warps 0-3.
 template <int RAD, typename T>
-__global__ void __launch_bounds__(NTHREADS, 1)
-fbf_tc_kernel(const __grid_constant__ DeviceParams p, const Work w, const Scratch sc) {
+__device__ __forceinline__ void load_taps(const DeviceParams& p, unsigned char* sGy, unsigned char* sGl,
+                                          uint32_t tmem, int tid) {
+  constexpr int NPART = Parts<T>::value;
+  using C = TcCfg<RAD, NPART>;
+  for (int i = tid; i < TILE_Y * (C::KY / 4); i += NCT) {
+    const int o = i / (C::KY / 4), k4 = (i - o * (C::KY / 4)) * 4;
+    uint32_t v[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int d = k4 + j - o;   // tap index 0..2r
+      v[j] = to_tf32((d >= 0 && d <= 2 * RAD) ? p.g[d] : 0.f);
+    }
+    *reinterpret_cast<uint4*>(sGy + off32<C::KY>(o, k4)) = make_uint4(v[0], v[1], v[2], v[3]);
+  }
+  if (NPART == 2) {
+    for (int i = tid; i < TILE_X * (C::KX / 8); i += NCT) {
+      const int o = i / (C::KX / 8), k8 = (i - o * (C::KX / 8)) * 8;
+      float v[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int d = k8 + j - o;
+        const float gv = (d >= 0 && d <= 2 * RAD) ? p.g[d] : 0.f;
+        v[j] = gv - round16<T>(gv);
+      }
+      *reinterpret_cast<uint4*>(sGl + off16<C::KX>(o, k8)) =
+          make_uint4(pack2<T>(v[0], v[1]), pack2<T>(v[2], v[3]), pack2<T>(v[4], v[5]), pack2<T>(v[6], v[7]));
+    }
+  }
+  const int warp = tid >> 5, lane = tid & 31;
+  if (warp < 4) {
+    const int o = 32 * warp + lane;
+    for (int j0 = 0; j0 < C::KX / 2; j0 += 8) {
+      uint32_t v[8];
+#pragma unroll
+      for (int jj = 0; jj < 8; ++jj) {
+        const int d0 = 2 * (j0 + jj) - o, d1 = d0 + 1;
+        v[jj] = pack2<T>((d0 >= 0 && d0 <= 2 * RAD) ? p.g[d0] : 0.f, (d1 >= 0 && d1 <= 2 * RAD) ? p.g[d1] : 0.f);
+      }
+      tmem_st8(tmem + ((uint32_t)(32 * warp) << 16) + C::GXC + j0, v);
+    }
+    tmem_wait_st();
+  }
+  proxy_fence();
+  tc_fence_before();
+}
+
+// The kernel body over a source of images (one image, or a device work-list of images of the
+// same radius class whose parameters may differ).
+template <int RAD, typename T, class Src>
+__device__ __forceinline__ void tc_body(const Src& src, const Scratch& sc) {
   constexpr int NPART = Parts<T>::value;
   using C = TcCfg<RAD, NPART>;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -476,31 +528,7 @@ fbf_tc_kernel(const __grid_constant__ DeviceParams p, const Work w, const Scratc
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-  // ---- set-up: Gy (TF32, shared memory), barriers, TMEM, Gx (tensor memory) ----------------
-  for (int i = tid; i < TILE_Y * (C::KY / 4); i += NTHREADS) {
-    const int o = i / (C::KY / 4), k4 = (i - o * (C::KY / 4)) * 4;
-    uint32_t v[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int d = k4 + j - o;   // tap index 0..2r
-      v[j] = to_tf32((d >= 0 && d <= 2 * RAD) ? p.g[d] : 0.f);
-    }
-    *reinterpret_cast<uint4*>(sGy + off32<C::KY>(o, k4)) = make_uint4(v[0], v[1], v[2], v[3]);
-  }
-  if (NPART == 2) {
-    for (int i = tid; i < TILE_X * (C::KX / 8); i += NTHREADS) {
-      const int o = i / (C::KX / 8), k8 = (i - o * (C::KX / 8)) * 8;
-      float v[8];
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const int d = k8 + j - o;
-        const float gv = (d >= 0 && d <= 2 * RAD) ? p.g[d] : 0.f;
-        v[j] = gv - round16<T>(gv);
-      }
-      *reinterpret_cast<uint4*>(sGl + off16<C::KX>(o, k8)) =
-          make_uint4(pack2<T>(v[0], v[1]), pack2<T>(v[2], v[3]), pack2<T>(v[4], v[5]), pack2<T>(v[6], v[7]));
-    }
-  }
+  // ---- set-up: barriers, TMEM (the taps are loaded per image by the compute warps) ----------
   if (tid == 0) {
     for (int i = 0; i < C::NSLOT; ++i) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(bFull + i)), "r"(NCW));
@@ -523,35 +551,14 @@ fbf_tc_kernel(const __grid_constant__ DeviceParams p, const Work w, const Scratc
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *sTmem;
-  if (warp < 4) {
-    // Gx[x', hx] = g(hx - x' - r) in lanes x' = 32 warp + lane, two K elements per column
-    const int o = 32 * warp + lane;
-    for (int j0 = 0; j0 < C::KX / 2; j0 += 8) {
-      uint32_t v[8];
-#pragma unroll
-      for (int jj = 0; jj < 8; ++jj) {
-        const int d0 = 2 * (j0 + jj) - o, d1 = d0 + 1;
-        v[jj] = pack2<T>((d0 >= 0 && d0 <= 2 * RAD) ? p.g[d0] : 0.f, (d1 >= 0 && d1 <= 2 * RAD) ? p.g[d1] : 0.f);
-      }
-      tmem_st8(tmem + ((uint32_t)(32 * warp) << 16) + C::GXC + j0, v);
-    }
-    tmem_wait_st();
-  }
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
 
   // ---- this CTA's share of the weighted (tile, term) sequence --------------------------------
-  const SingleSrc src{&p, w};
   const int G = gridDim.x;
   const int cta = blockIdx.x;
   int img0, img_end;
   long long u0, u_end;
   locate(src, ceil_div_ll((long long)cta * sc.wtot, G), sc.wtot, img0, u0);
   locate(src, ceil_div_ll((long long)(cta + 1) * sc.wtot, G), sc.wtot, img_end, u_end);
-  const int K = w.K, H = w.H, W = w.W;
-  const long long pitch = w.pitch;
-  const long long nunits = w.tiles * K;
 
   if (warp == NCW) {
     // ===================== MMA issuer ======================================================
@@ -572,6 +579,8 @@ fbf_tc_kernel(const __grid_constant__ DeviceParams p, const Work w, const Scratc
       int img = img0;
       long long u = u0;
       while (!ab && (img < img_end || (img == img_end && u < u_end))) {
+        const Work wk = src.work(img);
+        const int K = wk.K;
         const long long t = u / K;
         const int kb = (int)(u - t * K);
         const int ke = (img == img_end && t == u_end / K) ? (int)(u_end - t * K) : K;
@@ -618,7 +627,7 @@ fbf_tc_kernel(const __grid_constant__ DeviceParams p, const Work w, const Scratc
           }
         }
         u = t * K + ke;
-        if (u >= nunits) { ++img; u = 0; }
+        if (u >= wk.tiles * K) { ++img; u = 0; }
       }
       if (ab && lane == 0) *sAbort = 1;
       // every MMA this thread issued has completed before TMEM is released
@@ -631,8 +640,6 @@ fbf_tc_kernel(const __grid_constant__ DeviceParams p, const Work w, const Scratc
     const int q = warp & 3;              // TMEM lane quarter: output columns x' = 32 q + lane
     const int rg = warp >> 2;            // output rows y' = 16 rg .. 16 rg + 15
     const int ox = 32 * q + lane, oy0 = PX * rg;
-    const float m = p.center;
-    const float vmax = (float)min(p.R, 255);
     const uint32_t tq = tmem + ((uint32_t)(32 * q) << 16) + C::D2C + PX * rg;
     uint32_t P = 0;
     int slot = 0, ring = 0;              // ring slot and use count of the next chunk
@@ -640,6 +647,9 @@ fbf_tc_kernel(const __grid_constant__ DeviceParams p, const Work w, const Scratc
     int img = img0;
     long long u = u0;
     float nm[PX], dn[PX];
+    const DeviceParams* cp = nullptr;    // the current fragment's image parameters and record
+    Work cw{};
+    int cur_pidx = -1;                   // parameters whose taps are loaded
 
     // D1 of image s rounded to nearest TF32 in place: the y pass reads its A operand from
     // tensor memory as TF32, which drops the low mantissa bits (truncation); rounding first
@@ -680,7 +690,7 @@ fbf_tc_kernel(const __grid_constant__ DeviceParams p, const Work w, const Scratc
 #pragma unroll
       for (int ii = 0; ii < 8; ++ii)
         wv[ii] = tile_int ? __uint_as_float(wt[own[ii * C::FHS]])
-                          : fold_weight_slow(p, k, kind, w.in, pitch, H, W, ty0 + oy0 + h + ii, tx0 + ox);
+                          : fold_weight_slow(*cp, k, kind, cw.in, cw.pitch, cw.H, cw.W, ty0 + oy0 + h + ii, tx0 + ox);
     };
     auto fold = [&](uint32_t Pf, int k, int kind, bool tile_int, int tx0, int ty0, const uint32_t* wt) {
       float wv[8];
@@ -706,12 +716,22 @@ fbf_tc_kernel(const __grid_constant__ DeviceParams p, const Work w, const Scratc
     };
 
     while (img < img_end || (img == img_end && u < u_end)) {
+      cw = src.work(img);
+      cp = &src.params(img);
+      const int K = cw.K, H = cw.H, W = cw.W;
+      const long long pitch = cw.pitch;
+      const float m = cp->center;
+      const float vmax = (float)min(cp->R, 255);
+      if (cw.param_idx != cur_pidx) {   // this image's taps (the previous fragment's MMAs are complete)
+        load_taps<RAD, T>(*cp, sGy, sGl, tmem, tid);
+        cur_pidx = cw.param_idx;
+      }
       const long long t = u / K;
       const int kb = (int)(u - t * K);
       const int ke = (img == img_end && t == u_end / K) ? (int)(u_end - t * K) : K;
       const int np = frag_pairs(kb, ke);
-      const int tx0 = (int)(t % w.tiles_x) * TILE_X;
-      const int ty0 = (int)(t / w.tiles_x) * TILE_Y;
+      const int tx0 = (int)(t % cw.tiles_x) * TILE_X;
+      const int ty0 = (int)(t / cw.tiles_x) * TILE_Y;
 
       // f of the tile + halo as bytes (zero outside the image and in the padding); the tile
       // takes the table path when every pixel is an integer in [0, min(R, 255)]
@@ -725,7 +745,7 @@ fbf_tc_kernel(const __grid_constant__ DeviceParams p, const Work w, const Scratc
         for (int j = 0; j < 4; ++j) {
           const int gx = tx0 - RAD + hx + j;
           if (hy < C::HY && hx + j < C::HX && gy >= 0 && gy < H && gx >= 0 && gx < W) {
-            const float v = __ldg(w.in + (long long)gy * pitch + gx);
+            const float v = __ldg(cw.in + (long long)gy * pitch + gx);
             ok &= (v == rintf(v)) & (v >= 0.f) & (v <= vmax);
             word |= (uint32_t)(int)fminf(fmaxf(v, 0.f), 255.f) << (8 * j);
           }
@@ -744,14 +764,14 @@ fbf_tc_kernel(const __grid_constant__ DeviceParams p, const Work w, const Scratc
         // the term's tables are built at its first pair; slot k & 1 is free by then (its
         // previous term was last read by a fold before the previous pair's barrier)
         uint32_t* tslot = sTab + (k & 1) * C::TABW + (kind == 2 ? C::GENW : 0);
-        if (tile_int && kind != 2) build_term_table<T, NPART>(p, k, sTab + (k & 1) * C::TABW, tid);
+        if (tile_int && kind != 2) build_term_table<T, NPART>(*cp, k, sTab + (k & 1) * C::TABW, tid);
         ab = sync_compute_or(ab || *sAbort);   // also publishes the table
         if (ab) break;
         // a ring slot is free once the x pass has consumed the chunk it held NSLOT chunks ago
         for (int c = 0; c < C::NC; ++c) {
           if (ring > 0 && !mbar_wait(bEmpty + slot, (ring - 1) & 1, sAbort)) { ab = true; *sAbort = 1; }
-          gen_chunk<RAD, T>(sBh + slot * C::SLOTB, c, sFh, tslot, tile_int, interior, tx0, ty0, H, W, w.in,
-                            pitch, k, kind, p, tid);
+          gen_chunk<RAD, T>(sBh + slot * C::SLOTB, c, sFh, tslot, tile_int, interior, tx0, ty0, H, W, cw.in,
+                            pitch, k, kind, *cp, tid);
           proxy_fence();
           __syncwarp();
           if (lane == 0) mbar_arrive(bFull + slot);
@@ -773,7 +793,7 @@ fbf_tc_kernel(const __grid_constant__ DeviceParams p, const Work w, const Scratc
       bool finish = true;
       if (!(kb == 0 && ke == K)) {
         const int wmine = term_start(ke) - term_start(kb);
-        const int pslot = (u0 / K == t && img == img0) ? 0 : 1;
+        const int pslot = (img == img0 && u0 / K == t) ? 0 : 1;
         float* pp = sc.partial + ((long long)(cta * 2 + pslot) * 2) * PX * NCT;
 #pragma unroll
         for (int a = 0; a < PX; ++a) {
@@ -783,14 +803,14 @@ fbf_tc_kernel(const __grid_constant__ DeviceParams p, const Work w, const Scratc
         __threadfence();
         sync_compute();
         if (tid == 0) {
-          const int prev = atomicAdd(sc.counter + t, wmine);
-          *sFin = (prev + wmine == w.wtile);
+          const int prev = atomicAdd(sc.counter + cw.counter_base + t, wmine);
+          *sFin = (prev + wmine == cw.wtile);
         }
         sync_compute();
         finish = *sFin != 0;
         if (finish) {
           __threadfence();
-          const long long g0 = t * w.wtile;
+          const long long g0 = cw.wstart + t * cw.wtile;
           const long long c0 = g0 * G / sc.wtot;
           const long long c1 = (g0 + term_start(K - 1)) * G / sc.wtot;
 #pragma unroll
@@ -801,7 +821,7 @@ fbf_tc_kernel(const __grid_constant__ DeviceParams p, const Work w, const Scratc
             locate(src, ceil_div_ll(cc * sc.wtot, G), sc.wtot, fi, fu);
             locate(src, ceil_div_ll((cc + 1) * sc.wtot, G), sc.wtot, gi, gu);
             if (!(fi < gi || (fi == gi && fu < gu))) continue;
-            const int sl = (fu / K == t) ? 0 : 1;
+            const int sl = (fi == img && fu / K == t) ? 0 : 1;
             const float* qp = sc.partial + ((cc * 2 + sl) * 2) * PX * NCT;
 #pragma unroll
             for (int a = 0; a < PX; ++a) {
@@ -809,7 +829,7 @@ fbf_tc_kernel(const __grid_constant__ DeviceParams p, const Work w, const Scratc
               dn[a] += __ldcg(qp + (PX + a) * NCT + tid);
             }
           }
-          if (tid == 0) sc.counter[t] = 0;
+          if (tid == 0) sc.counter[cw.counter_base + t] = 0;
         }
       }
       if (finish) {
@@ -820,14 +840,14 @@ fbf_tc_kernel(const __grid_constant__ DeviceParams p, const Work w, const Scratc
             const int gy = ty0 + oy0 + a;
             if (gy < H) {
               const float d = dn[a];
-              const float f = __ldg(w.in + (long long)gy * pitch + gx);
-              w.out[(long long)gy * pitch + gx] = (d > 0.f) ? m + nm[a] / d : f;
+              const float f = __ldg(cw.in + (long long)gy * pitch + gx);
+              cw.out[(long long)gy * pitch + gx] = (d > 0.f) ? m + nm[a] / d : f;
             }
           }
         }
       }
       u = t * K + ke;
-      if (u >= nunits) { ++img; u = 0; }
+      if (u >= cw.tiles * K) { ++img; u = 0; }
       sync_compute();   // sFh and the finish flag are rewritten by the next fragment
     }
     if (ab) *sAbort = 1;
@@ -838,6 +858,22 @@ fbf_tc_kernel(const __grid_constant__ DeviceParams p, const Work w, const Scratc
   tc_fence_after();
   if (tid == 0 && *sAbort) atomicOr(&g_tc_error, 1);
   if (warp == NCW) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" :: "r"(tmem));
+}
+
+template <int RAD, typename T>
+__global__ void __launch_bounds__(NTHREADS, 1)
+fbf_tc_kernel(const __grid_constant__ DeviceParams p, const Work w, const Scratch sc) {
+  const SingleSrc src{&p, w};
+  tc_body<RAD, T>(src, sc);
+}
+
+// Batched form: the images of one radius class from a device work-list (parameters per plan
+// de-duplicated), one persistent stream-K launch over all of them.
+template <int RAD, typename T>
+__global__ void __launch_bounds__(NTHREADS, 1)
+fbf_tc_batch_kernel(const DeviceParams* __restrict__ prm, const Work* __restrict__ wl, int n, const Scratch sc) {
+  const ListSrc src{prm, wl, n};
+  tc_body<RAD, T>(src, sc);
 }
 
 template <int RAD, typename T>
@@ -893,6 +929,37 @@ int launch_rad(const DeviceParams& dp, const float* in, float* out, int H, int W
   if (e != cudaSuccess) return set_error(FBF_ECUDA, std::string("fbf_filter: launch: ") + cudaGetErrorString(e));
   return FBF_OK;
 }
+// Batched launch of one radius class (work-list already on the device).
+template <int RAD, typename T>
+int launch_batch_rad(const DeviceParams* dparams, const Work* dwork, int n, long long wtot, float* partial,
+                     int* counter, cudaStream_t st, int dev) {
+  using C = TcCfg<RAD, Parts<T>::value>;
+  static int sms[64] = {0};
+  if (dev < 0 || dev >= 64) return set_error(FBF_EUNSUPPORTED, "fbf_launch: device index >= 64");
+  if (!sms[dev]) {
+    cudaError_t e = cudaFuncSetAttribute(fbf_tc_batch_kernel<RAD, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    if (e != cudaSuccess) return set_error(FBF_ECUDA, std::string("fbf_launch: ") + cudaGetErrorString(e));
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fbf_tc_batch_kernel<RAD, T>, NTHREADS, C::SMEM);
+    if (e != cudaSuccess || occ != 1)
+      return set_error(FBF_ECUDA, "fbf_launch: tensor-core kernel needs exactly one CTA per SM");
+    int s = 0;
+    cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev);
+    sms[dev] = s;
+  }
+  long long G = sms[dev];
+  if (G > wtot) G = wtot;
+  if (G < 1) return FBF_OK;
+  Scratch sc{};
+  sc.wtot = wtot;
+  sc.partial = partial;
+  sc.counter = counter;
+  fbf_tc_batch_kernel<RAD, T><<<(unsigned)G, NTHREADS, C::SMEM, st>>>(dparams, dwork, n, sc);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return set_error(FBF_ECUDA, std::string("fbf_launch: ") + cudaGetErrorString(e));
+  return FBF_OK;
+}
+
 template <typename T>
 int launch_type(const DeviceParams& dp, const float* in, float* out, int H, int W, size_t pitch,
                 cudaStream_t st) {
@@ -910,6 +977,29 @@ int launch_tc(const DeviceParams& dp, const float* in, float* out, int H, int W,
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if (precision == FBF_BF16_TC) return tc::launch_type<__nv_bfloat16>(dp, in, out, H, W, pitch, st);
   return tc::launch_type<__half>(dp, in, out, H, W, pitch, st);
+}
+
+int launch_tc_batch(int rad, int precision, const DeviceParams* dparams, const fp32::Work* dwork, int n, long long wtot,
+                    float* partial, int* counter, void* stream, int dev) {
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const bool bf = precision == FBF_BF16_TC;
+  switch (rad) {
+    case 6: return bf ? tc::launch_batch_rad<6, __nv_bfloat16>(dparams, dwork, n, wtot, partial, counter, st, dev)
+                      : tc::launch_batch_rad<6, __half>(dparams, dwork, n, wtot, partial, counter, st, dev);
+    case 15: return bf ? tc::launch_batch_rad<15, __nv_bfloat16>(dparams, dwork, n, wtot, partial, counter, st, dev)
+                       : tc::launch_batch_rad<15, __half>(dparams, dwork, n, wtot, partial, counter, st, dev);
+    case 30: return bf ? tc::launch_batch_rad<30, __nv_bfloat16>(dparams, dwork, n, wtot, partial, counter, st, dev)
+                       : tc::launch_batch_rad<30, __half>(dparams, dwork, n, wtot, partial, counter, st, dev);
+    default: return set_error(FBF_EUNSUPPORTED, "fbf_launch: no tensor-core radius class");
+  }
+}
+
+int tc_batch_partial_bytes(int dev, size_t* out) {
+  int s = 0;
+  cudaError_t e = cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return set_error(FBF_ECUDA, std::string("fbf_launch: ") + cudaGetErrorString(e));
+  *out = (size_t)s * 2 * 2 * tc::PX * tc::NCT * sizeof(float);
+  return FBF_OK;
 }
 
 int device_errors(int* flags, int clear) {

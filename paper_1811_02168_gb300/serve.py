@@ -149,9 +149,11 @@ class Server:
 
 class TorchBackend:
     """Device backend on the library's batched path: inputs copied on a copy stream,
-    one batched launch per server launch on the compute stream, results copied back."""
+    one batched launch per server launch on the compute stream, results copied back.
+    ``precision`` selects the form every request is filtered in (FBF_FP32, FBF_FP16_TC,
+    FBF_BF16_TC)."""
 
-    def __init__(self, binding, device=0):
+    def __init__(self, binding, device=0, precision=0):
         import torch
         self.torch = torch
         self.B = binding
@@ -159,12 +161,13 @@ class TorchBackend:
         self.copy = torch.cuda.Stream(self.dev)
         self.compute = torch.cuda.Stream(self.dev)
         self.plans = {}
+        self.precision = precision
         self.batch = binding.Batch(4096)
 
     def plan(self, theta, sigma, K):
         key = (theta, sigma, K)
         if key not in self.plans:
-            self.plans[key] = self.B.Plan(sigma, 255, theta, K=K)
+            self.plans[key] = self.B.Plan(sigma, 255, theta, K=K, precision=self.precision)
         return self.plans[key]
 
     def admit(self, r: Request):

@@ -129,3 +129,56 @@ def test_launches_in_a_row_reuse_the_work_list_ring(B):
     for x, y in zip(xs, ys):
         assert float((y - _single(B, plan, x)).abs().max()) <= TOL
     batch.close()
+
+
+@pytest.mark.parametrize("form", ["fp16", "bf16"])
+def test_tensor_core_forms_in_the_batch(B, form):
+    """Tensor-core plans share a batch with FP32 plans (one launch per form and radius class);
+    each tensor-core image equals the same image filtered alone by fbf_filter (the per-tile
+    arithmetic is identical; only the order of split-tile partial sums may differ) and
+    meets the 0.5 gray-level bound against the oracle."""
+    prec = B.FBF_FP16_TC if form == "fp16" else B.FBF_BF16_TC
+    jobs = _mixed_jobs(12, 21 if form == "fp16" else 22)
+    batch = B.Batch(32)
+    plans, items = {}, []
+    for n, (H, W, theta, sigma, K, seed) in enumerate(jobs):
+        p_here = prec if n % 3 else B.FBF_FP32
+        key = (theta, sigma, K, p_here)
+        if key not in plans:
+            plans[key] = B.Plan(sigma, 255, theta, K=K, precision=p_here)
+        img = voronoi_image(H, W, 8, 30.0, 10.0, seed=seed)
+        x = torch.from_numpy(img).cuda()
+        y = torch.full_like(x, -5.0)
+        items.append((img, plans[key], x, y, _single(B, plans[key], x), theta, sigma, K, p_here))
+        batch.submit(plans[key], x, y)
+    batch.launch()
+    torch.cuda.synchronize()
+    for img, plan, x, y, ref, theta, sigma, K, p_here in items:
+        assert float((y - ref).abs().max()) <= TOL
+        if p_here != B.FBF_FP32 and img.size <= 60000:
+            op = ofit.make_plan(sigma, 255, K=K)
+            exact = ofl.fourier_bf(img.astype(np.float64), theta, op.c, op.T)
+            assert np.abs(y.cpu().numpy() - exact).max() <= 0.5
+    assert B.fbf_device_errors(True) == 0
+    batch.close()
+
+
+def test_tensor_core_batch_graph_replay(B):
+    jobs = _mixed_jobs(5, 31)
+    batch = B.Batch(8)
+    items = []
+    for H, W, theta, sigma, K, seed in jobs:
+        plan = B.Plan(sigma, 255, theta, K=K, precision=B.FBF_BF16_TC)
+        x = torch.from_numpy(voronoi_image(H, W, 8, 30.0, 10.0, seed=seed)).cuda()
+        y = torch.empty_like(x)
+        batch.submit(plan, x, y)
+        items.append((plan, x, y, H, W))
+    batch.capture()
+    for rep in range(2):
+        for i, (plan, x, y, H, W) in enumerate(items):
+            x.copy_(torch.from_numpy(voronoi_image(H, W, 8, 30.0, 10.0, seed=500 * rep + i)).cuda())
+        t = batch.replay()
+        batch.wait(t, 60.0)
+        for plan, x, y, H, W in items:
+            assert float((y - _single(B, plan, x)).abs().max()) <= TOL
+    batch.close()

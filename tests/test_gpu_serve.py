@@ -1,6 +1,8 @@
 """Served requests on the GPU: each result equals the same request filtered alone by
 fbf_filter, within the FP32 tolerance, although it was batched with whatever else had
-arrived (continuous batching) and its copies overlapped other launches."""
+arrived (continuous batching) and its copies overlapped other launches.  Both the FP32 form
+and the compensated BF16 tensor-core form (config 4's served form): only the order of
+split-tile partial sums can differ between a batched and a lone launch."""
 import numpy as np
 import pytest
 
@@ -23,7 +25,8 @@ def B():
     return binding
 
 
-def test_served_results_equal_alone_results(B):
+@pytest.mark.parametrize("form", ["fp32", "bf16_tc"])
+def test_served_results_equal_alone_results(B, form):
     rng = np.random.default_rng(77)
     reqs = []
     t = 0.0
@@ -38,7 +41,7 @@ def test_served_results_equal_alone_results(B):
         r.host_in = torch.from_numpy(img).pin_memory()
         r.host_out = torch.empty((H, W), dtype=torch.float32).pin_memory()
         reqs.append(r)
-    be = TorchBackend(B)
+    be = TorchBackend(B, precision=B.FBF_FP32 if form == "fp32" else B.FBF_BF16_TC)
     st = Server(be, hbm_budget_bytes=1 << 30, max_batch=8, max_inflight=2).run(reqs)
     assert st.requests == len(reqs)
     assert st.launches < len(reqs)          # requests were batched
