@@ -48,6 +48,20 @@ def _args():
     return ap.parse_args()
 
 
+def _job_rate(px_per_rank_step: float, steps: int, local_s: float, world: int, device=None):
+    """Whole-job Mpix/s when each of `world` ranks filters the same per-rank work (weak
+    scaling, no data-path collective): the job takes as long as its slowest rank, found with
+    one MAX all-reduce of the elapsed time.  Returns (Mpix/s, job seconds)."""
+    t = float(local_s)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        tt = torch.tensor([t], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    return world * px_per_rank_step * steps / t / 1e6, t
+
+
 def _jobs(name):
     from paper_1811_02168_gb300 import synth
     if name == "batch":
@@ -315,12 +329,8 @@ def run_ours(a):
     step_ms = [b.elapsed_time(e) for b, e in st_ev]
     launch_ms = [statistics.mean(ln_ev[s][i][0].elapsed_time(ln_ev[s][i][1]) for s in range(a.steps))
                  for i in range(len(jobs))]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * px_step * a.steps / (total_ms / 1e3) / 1e6
+    value, total_s = _job_rate(px_step, a.steps, sum(step_ms) / 1e3, world, dev)
+    total_ms = 1e3 * total_s
 
     # ---- end to end through the public API with host buffers --------------------------
     host_in = {s: torch.from_numpy(v).pin_memory() for s, v in imgs_np.items()}
@@ -337,12 +347,7 @@ def run_ours(a):
         for i, (p, j) in enumerate(zip(plans, jobs)):
             B.bilateral_filter(p, host_in[j.seed], out=host_out[i])
         e2e_t.append(time.perf_counter() - t0)
-    e2e_sec = sum(e2e_t)
-    if world > 1:
-        t = torch.tensor([e2e_sec], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_sec = float(t.item())
-    e2e_val = world * px_step * e2e_steps / e2e_sec / 1e6
+    e2e_val, _ = _job_rate(px_step, e2e_steps, sum(e2e_t), world, dev)
     h2d = sum(4 * j.H * j.W for j in jobs)
     d2h = sum(4 * j.H * j.W for j in jobs)
     clk = clocks.stop() if rank == 0 else None
