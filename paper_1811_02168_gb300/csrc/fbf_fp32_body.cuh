@@ -233,6 +233,7 @@ __device__ __forceinline__ void fbf_body(const Src& src, const Scratch& sc) {
     // integers in [0, min(R, TABN-1)] (8-bit images), else the sincospi path.
     const float vmax = (float)min(p.R, TABN - 1);
     int ok = 1;
+#pragma unroll 4
     for (int i = tid; i < C::HROWS_P * C::TXH; i += NT) {
       const int row = i / C::TXH, xx = i - row * C::TXH;
       const int gy = ty0 - RAD + row, gx = tx0 - RAD + xx;
