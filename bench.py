@@ -471,9 +471,12 @@ def run_psnr(a):
 
     import __graft_entry__
     __graft_entry__.build()
-    from oracle import filters as ofl
     from paper_1811_02168_gb300 import binding as B
     from paper_1811_02168_gb300 import synth
+
+    def psnr(a, b):   # Section III: 10 log10(255^2 / MSE)
+        mse = float(np.mean((np.asarray(a, np.float64) - np.asarray(b, np.float64)) ** 2))
+        return math.inf if mse == 0 else 10.0 * math.log10(255.0 * 255.0 / mse)
 
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
@@ -511,7 +514,7 @@ def run_psnr(a):
                 if m == "proposed":
                     t_four += dt
                 launches += 3
-                ps[m].append(ofl.psnr(y.cpu().numpy(), ref))
+                ps[m].append(psnr(y.cpu().numpy(), ref))
         rows.append({"theta": th, "sigma": sg, "K": K, "T_proposed": plans["proposed"].T,
                      "psnr_db": {m: float(np.mean(v)) for m, v in ps.items()}})
         for p in plans.values():
