@@ -179,15 +179,19 @@ def _traffic_for(kernel: str):
     return None
 
 
-def _tc_mma_flops(K: int, r: int, H: int, W: int) -> float:
+def _tc_mma_flops(K: int, r: int, H: int, W: int, compensated: bool = False) -> float:
     """FP16-equivalent dense MMA flops one tensor-core launch executes (banded Toeplitz
-    contractions, padding included; the TF32 y pass counts twice, at half the FP16 rate)."""
+    contractions, padding included; TF32 counts twice, at half the FP16 rate).  The
+    compensated BF16 form runs three x-pass products, a 32-row tile at r > 15, and an extra
+    FP16 y pass for the low part of the x-pass result."""
     R = 6 if r <= 6 else 15 if r <= 15 else 30
+    ty = 32 if (compensated and R > 15) else 64
     kx = (128 + 2 * R + 15) // 16 * 16
-    ky = (64 + 2 * R + 15) // 16 * 16
-    tiles = math.ceil(W / 128) * math.ceil(H / 64)
-    per_image = 2 * 128 * ky * kx + 2 * (2 * 128 * 64 * ky)
-    return tiles * (4 * K - 2) * per_image
+    ky = (ty + 2 * R + 15) // 16 * 16
+    tiles = math.ceil(W / 128) * math.ceil(H / ty)
+    x = 2 * 128 * ky * kx * (3 if compensated else 1)
+    y = 2 * (2 * 128 * ty * ky) + (2 * 128 * ty * ky if compensated else 0)
+    return tiles * (4 * K - 2) * (x + y)
 
 
 _ORACLE_PLANS = {}
@@ -443,7 +447,7 @@ def _forms(a, B, jobs, plans, x, fp32_launch_ms, refs, flush, stream, dev):
         errs = [float(np.abs(y[: r.shape[0]].cpu().numpy() - r).max()) for y, r in zip(ys, refs)]
         peak = _bf16_peak()
         alg = sum(_flops_per_px(p.K, p.radius) * j.H * j.W for p, j in zip(tp, jobs)) / (ms / 1e3) / 1e12
-        dense = sum(_tc_mma_flops(p.K, p.radius, j.H, j.W) for p, j in zip(tp, jobs)) / (ms / 1e3) / 1e12
+        dense = sum(_tc_mma_flops(p.K, p.radius, j.H, j.W, name == "bf16_tc") for p, j in zip(tp, jobs)) / (ms / 1e3) / 1e12
         tr = _traffic_for("fbf_tc_kernel")
         forms[name] = {"mpix_s": px / (ms / 1e3) / 1e6, "kernel_ms": ms, "max_abs_err": max(errs),
                        "per_image_err": errs, "tolerance": TOL_TC, "meets_tolerance": max(errs) <= TOL_TC,

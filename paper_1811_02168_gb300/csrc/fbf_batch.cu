@@ -114,7 +114,7 @@ int tc_launch(const DeviceParams* dparams, const Work* dwork, int n, long long w
 }
 template <int RAD, int PREC>
 ClassLaunch tc_entry(const char* name) {
-  ClassLaunch c{&tc_launch<RAD, PREC>, &tc_batch_partial_bytes, 64, name};
+  ClassLaunch c{&tc_launch<RAD, PREC>, &tc_batch_partial_bytes, tc_tile_rows(RAD, PREC), name};
   c.TX = 128;
   return c;
 }

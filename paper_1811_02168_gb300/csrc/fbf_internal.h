@@ -91,6 +91,7 @@ namespace fp32 { struct Work; }
 int launch_tc_batch(int rad, int precision, const DeviceParams* dparams, const fp32::Work* dwork, int n,
                     long long wtot, float* partial, int* counter, void* stream, int dev);
 int tc_batch_partial_bytes(int dev, size_t* out);
+int tc_tile_rows(int rad, int precision);   // output tile height of a tensor-core configuration
 // Same kernel, scratch from a fixed device array instead of the per-stream workspace.
 int launch_fp32_noalloc(const DeviceParams& dp, const float* in, float* out, int H, int W,
                         size_t pitch, void* stream);

@@ -56,11 +56,11 @@ using fp32::term_cs_any;
 __device__ int g_tc_error;   // bit 0: an mbarrier wait gave up
 
 constexpr int TILE_X = 128;             // output tile width  = TMEM lanes = MMA M
-constexpr int TILE_Y = 64;              // output tile height = y-pass N
+constexpr int TILE_Y_MAX = 64;          // output tile height = y-pass N (per configuration: TcCfg::TY)
 constexpr int NCW = 16;                 // compute warps: 4 TMEM lane quarters x 4 row groups
 constexpr int NCT = NCW * 32;           // compute threads
 constexpr int NTHREADS = NCT + 32;      // + the MMA-issuing warp
-constexpr int PX = TILE_Y / 4;          // output pixels per compute thread (one column)
+constexpr int PX_MAX = TILE_Y_MAX / 4;  // output pixels per compute thread (one column)
 constexpr int kWaitLimit = 1 << 22;
 
 // FBF_BF16_TC stores every operand value and every x-pass tap as a compensated pair of BF16
@@ -74,9 +74,14 @@ template <int RAD, int NPART>
 struct TcCfg {
   static constexpr int HX = TILE_X + 2 * RAD;             // halo columns
   static constexpr int KX = (HX + 15) / 16 * 16;          // x-pass K
-  static constexpr int HY = TILE_Y + 2 * RAD;             // halo rows
+  // tile height: 64; 32 for the compensated form at r > 15, where the split x-pass result
+  // (below) needs the tensor-memory columns of a taller tile
+  static constexpr int TY = (NPART == 2 && RAD > 15) ? 32 : TILE_Y_MAX;
+  static constexpr int PX = TY / 4;                       // output pixels per compute thread
+  static constexpr int HY = TY + 2 * RAD;                 // halo rows
   static constexpr int KY = (HY + 15) / 16 * 16;          // x-pass N = y-pass K
-  static constexpr int GYB = TILE_Y * KY * 4;             // Gy, TF32 (shared memory)
+  static constexpr int GYB = TY * KY * 4;                 // Gy, TF32 (shared memory)
+  static constexpr int GY16B = NPART == 2 ? TY * KY * 2 : 0;   // Gy, FP16: the lo part's y pass
   static constexpr int GLB = NPART == 2 ? TILE_X * KX * 2 : 0;   // Gx_lo (shared memory)
   // B_h is produced as NC column chunks of CK x-pass K-steps (16 columns each) into a ring of
   // NSLOT chunk slots, each holding the chunk of both images of a pair (and of both parts of
@@ -95,7 +100,7 @@ struct TcCfg {
   static constexpr int TABW = 2 * GENW + 512;             // words per term-table slot
   static constexpr int TABB = 2 * TABW * 4;               // 2 slots (terms k even / odd)
   static constexpr int BARB = 256;
-  static constexpr int FIXED = GYB + GLB + FHB + TABB + BARB + 1024;
+  static constexpr int FIXED = GYB + GY16B + GLB + FHB + TABB + BARB + 1024;
   static constexpr int NSLOT0 = (232448 - FIXED) / SLOTB;
   static constexpr int NSLOT = NSLOT0 < 2 * NC ? NSLOT0 : 2 * NC;
   static constexpr int SMEM = FIXED + NSLOT * SLOTB;
@@ -105,8 +110,12 @@ struct TcCfg {
   static constexpr int GXS = (KX / 2 + 31) / 32 * 32;
   static constexpr int D1S = (KY + 31) / 32 * 32;
   static constexpr int D1C = GXS;
-  static constexpr int D2C = D1C + 2 * D1S;
-  static_assert(D2C + 2 * TILE_Y <= 512, "TMEM columns");
+  // compensated form: the x-pass result splits into hi (TF32, in place) + lo (FP16 pairs,
+  // KY/2 columns per image) so that the y pass carries ~21 significant bits
+  static constexpr int D1LS = NPART == 2 ? (KY / 2 + 15) / 16 * 16 : 0;
+  static constexpr int D1LC = D1C + 2 * D1S;
+  static constexpr int D2C = D1LC + 2 * D1LS;
+  static_assert(D2C + 2 * TY <= 512, "TMEM columns");
   static_assert(NSLOT >= 1, "chunk ring");
   static_assert(SMEM <= 232448, "tensor-core tile does not fit in shared memory");
   static_assert(KY <= 256, "x-pass N exceeds one MMA");
@@ -280,6 +289,10 @@ __device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&r)[8])
   asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};"
                :: "r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]),
                   "r"(r[7]) : "memory");
+}
+__device__ __forceinline__ void tmem_st4(uint32_t taddr, const uint32_t (&r)[4]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};"
+               :: "r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]) : "memory");
 }
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
@@ -455,7 +468,7 @@ __device__ __forceinline__ void load_taps(const DeviceParams& p, unsigned char* 
                                           uint32_t tmem, int tid) {
   constexpr int NPART = Parts<T>::value;
   using C = TcCfg<RAD, NPART>;
-  for (int i = tid; i < TILE_Y * (C::KY / 4); i += NCT) {
+  for (int i = tid; i < C::TY * (C::KY / 4); i += NCT) {
     const int o = i / (C::KY / 4), k4 = (i - o * (C::KY / 4)) * 4;
     uint32_t v[4];
 #pragma unroll
@@ -464,6 +477,21 @@ __device__ __forceinline__ void load_taps(const DeviceParams& p, unsigned char* 
       v[j] = to_tf32((d >= 0 && d <= 2 * RAD) ? p.g[d] : 0.f);
     }
     *reinterpret_cast<uint4*>(sGy + off32<C::KY>(o, k4)) = make_uint4(v[0], v[1], v[2], v[3]);
+  }
+  if (NPART == 2) {   // FP16 copy of Gy for the y pass of the x-pass result's lo part
+    unsigned char* sGy16 = sGy + C::GYB;
+    for (int i = tid; i < C::TY * (C::KY / 8); i += NCT) {
+      const int o = i / (C::KY / 8), k8 = (i - o * (C::KY / 8)) * 8;
+      float v[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int d = k8 + j - o;
+        v[j] = (d >= 0 && d <= 2 * RAD) ? p.g[d] : 0.f;
+      }
+      *reinterpret_cast<uint4*>(sGy16 + off16<C::KY>(o, k8)) =
+          make_uint4(pack2<__half>(v[0], v[1]), pack2<__half>(v[2], v[3]), pack2<__half>(v[4], v[5]),
+                     pack2<__half>(v[6], v[7]));
+    }
   }
   if (NPART == 2) {
     for (int i = tid; i < TILE_X * (C::KX / 8); i += NCT) {
@@ -507,7 +535,7 @@ __device__ __forceinline__ void tc_body(const Src& src, const Scratch& sc) {
   // 1024-byte aligned base, kept as an offset into the shared array (shared address space)
   unsigned char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   unsigned char* sGy = base;                        // y-pass B operand
-  unsigned char* sGl = sGy + C::GYB;                // Gx_lo (compensated form)
+  unsigned char* sGl = sGy + C::GYB + C::GY16B;     // Gx_lo (compensated form; Gy16 before it)
   unsigned char* sBh = sGl + C::GLB;                // chunk ring of the x-pass B operands
   unsigned char* sFh = sBh + C::NSLOT * C::SLOTB;   // f of the halo tile (uint8)
   uint32_t* sTab = reinterpret_cast<uint32_t*>(sFh + C::FHB);   // 2 term-table slots
@@ -569,8 +597,10 @@ __device__ __forceinline__ void tc_body(const Src& src, const Scratch& sc) {
       auto wait_all = [&](uint64_t* bar, uint32_t par) { return __all_sync(0xffffffffu, mbar_wait(bar, par, sAbort)); };
       const uint32_t fmt = std::is_same<T, __nv_bfloat16>::value ? 1u : 0u;
       const uint32_t idX = instr_desc(fmt, TILE_X, C::KY);
-      const uint32_t idY = instr_desc(2u, TILE_X, TILE_Y);
+      const uint32_t idY = instr_desc(2u, TILE_X, C::TY);
+      const uint32_t idY16 = instr_desc(0u, TILE_X, C::TY);   // lo part: FP16 operands
       const uint64_t dGy = op_desc(smem_u32(sGy), 32 * C::KY);
+      const uint64_t dGy16 = op_desc(smem_u32(sGy + C::GYB), 16 * C::KY);
       const uint64_t dBh = op_desc(smem_u32(sBh), 16 * C::CW);
       const uint64_t dGl = op_desc(smem_u32(sGl), 16 * C::KX);
       uint32_t P = 0;
@@ -621,8 +651,14 @@ __device__ __forceinline__ void tc_body(const Src& src, const Scratch& sc) {
             tc_fence_after();
 #pragma unroll
             for (int ks = 0; ks < C::KY / 8; ++ks)
-              mma_ts_tf32(tmem + C::D2C + s * TILE_Y, tmem + C::D1C + s * C::D1S + 8 * ks,
+              mma_ts_tf32(tmem + C::D2C + s * C::TY, tmem + C::D1C + s * C::D1S + 8 * ks,
                           dGy + (uint64_t)(16 * ks), idY, ks > 0);
+            if (NPART == 2) {   // + Gy x lo (FP16 pairs, 16 K elements per 8 columns)
+#pragma unroll
+              for (int ks = 0; ks < C::KY / 16; ++ks)
+                mma_ts_f16(tmem + C::D2C + s * C::TY, tmem + C::D1LC + s * C::D1LS + 8 * ks,
+                           dGy16 + (uint64_t)(16 * ks), idY16, 1u);
+            }
             mma_commit_el(s ? bYb : bYa);
           }
         }
@@ -639,6 +675,7 @@ __device__ __forceinline__ void tc_body(const Src& src, const Scratch& sc) {
     // ===================== compute warps ==================================================
     const int q = warp & 3;              // TMEM lane quarter: output columns x' = 32 q + lane
     const int rg = warp >> 2;            // output rows y' = 16 rg .. 16 rg + 15
+    constexpr int PX = C::PX;
     const int ox = 32 * q + lane, oy0 = PX * rg;
     const uint32_t tq = tmem + ((uint32_t)(32 * q) << 16) + C::D2C + PX * rg;
     uint32_t P = 0;
@@ -658,6 +695,7 @@ __device__ __forceinline__ void tc_body(const Src& src, const Scratch& sc) {
       if (!mbar_wait(s ? bXb : bXa, Pr & 1, sAbort)) { ab = true; *sAbort = 1; }
       tc_fence_after();
       const uint32_t d1 = tmem + ((uint32_t)(32 * q) << 16) + C::D1C + s * C::D1S;
+      const uint32_t d1lo = tmem + ((uint32_t)(32 * q) << 16) + C::D1LC + s * C::D1LS;
       constexpr int NCH = C::KY / 8;
 #pragma unroll
       for (int c0 = 0; c0 < NCH; c0 += 8) {   // two chunks per warp at a time
@@ -672,9 +710,17 @@ __device__ __forceinline__ void tc_body(const Src& src, const Scratch& sc) {
         for (int jj = 0; jj < 2; ++jj) {
           const int c = c0 + rg + 4 * jj;
           if (c < NCH) {
+            uint32_t lo[4];
 #pragma unroll
-            for (int e = 0; e < 8; ++e) v[jj][e] = to_tf32(__uint_as_float(v[jj][e]));
+            for (int e = 0; e < 8; e += 2) {
+              const float x0 = __uint_as_float(v[jj][e]), x1 = __uint_as_float(v[jj][e + 1]);
+              v[jj][e] = to_tf32(x0);
+              v[jj][e + 1] = to_tf32(x1);
+              // the rounding error of hi, exact in FP32, as FP16 (used by the compensated form)
+              lo[e / 2] = pack2<__half>(x0 - __uint_as_float(v[jj][e]), x1 - __uint_as_float(v[jj][e + 1]));
+            }
             tmem_st8(d1 + 8 * c, v[jj]);
+            if (NPART == 2) tmem_st4(d1lo + 4 * c, lo);
           }
         }
       }
@@ -701,7 +747,7 @@ __device__ __forceinline__ void tc_body(const Src& src, const Scratch& sc) {
       for (int h = 0; h < PX; h += 8) {   // 8 rows at a time keeps the live registers low
         uint32_t a[8], b[8];
         tmem_ld8(tq + h, a);
-        tmem_ld8(tq + TILE_Y + h, b);
+        tmem_ld8(tq + C::TY + h, b);
         if (h > 0) weights8(h, k, kind, tile_int, tx0, ty0, wt, wv);
         tmem_wait_ld();
 #pragma unroll
@@ -731,7 +777,7 @@ __device__ __forceinline__ void tc_body(const Src& src, const Scratch& sc) {
       const int ke = (img == img_end && t == u_end / K) ? (int)(u_end - t * K) : K;
       const int np = frag_pairs(kb, ke);
       const int tx0 = (int)(t % cw.tiles_x) * TILE_X;
-      const int ty0 = (int)(t / cw.tiles_x) * TILE_Y;
+      const int ty0 = (int)(t / cw.tiles_x) * C::TY;
 
       // f of the tile + halo as bytes (zero outside the image and in the padding); the tile
       // takes the table path when every pixel is an integer in [0, min(R, 255)]
@@ -753,7 +799,7 @@ __device__ __forceinline__ void tc_body(const Src& src, const Scratch& sc) {
         *reinterpret_cast<uint32_t*>(sFh + 4 * i) = word;
       }
       const bool tile_int = sync_compute_and(ok != 0);
-      const bool interior = tx0 - RAD >= 0 && ty0 - RAD >= 0 && tx0 + TILE_X + RAD <= W && ty0 + TILE_Y + RAD <= H;
+      const bool interior = tx0 - RAD >= 0 && ty0 - RAD >= 0 && tx0 + TILE_X + RAD <= W && ty0 + C::TY + RAD <= H;
 #pragma unroll
       for (int i = 0; i < PX; ++i) { nm[i] = 0.f; dn[i] = 0.f; }
 
@@ -913,7 +959,7 @@ int launch_rad(const DeviceParams& dp, const float* in, float* out, int H, int W
   w.H = H;
   w.W = W;
   w.tiles_x = (W + TILE_X - 1) / TILE_X;
-  w.tiles_y = (H + TILE_Y - 1) / TILE_Y;
+  w.tiles_y = (H + C::TY - 1) / C::TY;
   w.K = dp.K;
   w.wtile = 2 * dp.K - 1;
   w.tiles = (long long)w.tiles_x * w.tiles_y;
@@ -921,7 +967,7 @@ int launch_rad(const DeviceParams& dp, const float* in, float* out, int H, int W
   sc.wtot = w.tiles * w.wtile;
   long long G = sms[dev];
   if (G > sc.wtot) G = sc.wtot;
-  const size_t partial_bytes = (size_t)G * 2 * 2 * PX * NCT * sizeof(float);
+  const size_t partial_bytes = (size_t)G * 2 * 2 * C::PX * NCT * sizeof(float);
   int rc = get_workspace(dev, st, partial_bytes, (size_t)w.tiles, &sc.partial, &sc.counter);
   if (rc != FBF_OK) return rc;
   fbf_tc_kernel<RAD, T><<<(unsigned)G, NTHREADS, C::SMEM, st>>>(p, w, sc);
@@ -994,11 +1040,20 @@ int launch_tc_batch(int rad, int precision, const DeviceParams* dparams, const f
   }
 }
 
+int tc_tile_rows(int rad, int precision) {
+  const bool bf = precision == FBF_BF16_TC;
+  switch (rad) {
+    case 6: return bf ? tc::TcCfg<6, 2>::TY : tc::TcCfg<6, 1>::TY;
+    case 15: return bf ? tc::TcCfg<15, 2>::TY : tc::TcCfg<15, 1>::TY;
+    default: return bf ? tc::TcCfg<30, 2>::TY : tc::TcCfg<30, 1>::TY;
+  }
+}
+
 int tc_batch_partial_bytes(int dev, size_t* out) {
   int s = 0;
   cudaError_t e = cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return set_error(FBF_ECUDA, std::string("fbf_launch: ") + cudaGetErrorString(e));
-  *out = (size_t)s * 2 * 2 * tc::PX * tc::NCT * sizeof(float);
+  *out = (size_t)s * 2 * 2 * tc::PX_MAX * tc::NCT * sizeof(float);
   return FBF_OK;
 }
 

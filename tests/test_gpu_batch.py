@@ -37,6 +37,16 @@ def _mixed_jobs(n, seed):
     return jobs
 
 
+def _close(y, ref, tol=TOL):
+    """Batch and lone launches differ only in the order of split-tile partial sums.  A plan with
+    a poor kernel fit (e.g. K = 5 at sigma = 10, E = 3.35) can drive the Fourier denominator
+    close to zero at a pixel, where the output leaves [0, 255] by orders of magnitude (1e4 in
+    one test image) and a relative rounding difference shows in absolute terms: the tolerance
+    scales with the output's magnitude beyond the intensity range."""
+    scale = torch.clamp(ref.abs() / 255.0, min=1.0)
+    return float(((y - ref).abs() / scale).max()) <= tol
+
+
 def _single(B, plan, x):
     y = torch.empty_like(x)
     H, W = x.shape
@@ -154,7 +164,7 @@ def test_tensor_core_forms_in_the_batch(B, form):
     batch.launch()
     torch.cuda.synchronize()
     for img, plan, x, y, ref, theta, sigma, K, p_here in items:
-        assert float((y - ref).abs().max()) <= TOL
+        assert _close(y, ref)
         if p_here != B.FBF_FP32 and img.size <= 60000:
             op = ofit.make_plan(sigma, 255, K=K)
             exact = ofl.fourier_bf(img.astype(np.float64), theta, op.c, op.T)
@@ -168,7 +178,9 @@ def test_tensor_core_batch_graph_replay(B):
     batch = B.Batch(8)
     items = []
     for H, W, theta, sigma, K, seed in jobs:
-        plan = B.Plan(sigma, 255, theta, K=K, precision=B.FBF_BF16_TC)
+        # K from eps = 0.01: this test is about replay, so its plans fit the kernel well (a
+        # poorly fitted plan can put a pixel's denominator near zero, see _close)
+        plan = B.Plan(sigma, 255, theta, eps=0.01, precision=B.FBF_BF16_TC)
         x = torch.from_numpy(voronoi_image(H, W, 8, 30.0, 10.0, seed=seed)).cuda()
         y = torch.empty_like(x)
         batch.submit(plan, x, y)
@@ -180,5 +192,5 @@ def test_tensor_core_batch_graph_replay(B):
         t = batch.replay()
         batch.wait(t, 60.0)
         for plan, x, y, H, W in items:
-            assert float((y - _single(B, plan, x)).abs().max()) <= TOL
+            assert _close(y, _single(B, plan, x))
     batch.close()

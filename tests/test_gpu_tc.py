@@ -6,7 +6,7 @@ pairs hi + lo (FBF_BF16_TC); its result is rounded to nearest TF32 for the y pas
 are TF32.  Tolerance: the 0.5 gray-level bound stated for the 16-bit stack.  The FP16 form
 meets it on these images (max ~0.13) but not everywhere: where the bilateral denominator is
 small (a pixel unlike its whole window, e.g. at theta 10, sigma 10, noise 15) FP16 operand
-rounding reaches ~1.8, which the compensated BF16 form brings to ~0.6 (test below).
+rounding reaches ~1.8; the compensated BF16 form stays near 0.05 there (test below).
 """
 import numpy as np
 import pytest
@@ -79,10 +79,9 @@ def test_tc_radius_limit(B):
 
 def test_bf16_compensated_on_small_denominators(B):
     """A 256 x 256 window of the 4096 x 4096 theta-10 workload image (noise 15) that holds
-    pixels whose bilateral denominator is near its minimum (the centre tap alone).  There
-    the remaining error of the compensated form is the TF32 rounding of the x-pass result
-    in the y pass (a CPU model of the arithmetic gives 0.59 here, 0.01 with that value split
-    too); FP16 operands give 1.78.  Checked against that measured limit, not the 0.5 bound."""
+    pixels whose bilateral denominator is near its minimum (the centre tap alone).  FP16
+    operands give 1.78 there; the compensated form (operands, taps and the x-pass result
+    split into hi + lo) stays within the 0.5 bound (a CPU model of its arithmetic: 0.01)."""
     from paper_1811_02168_gb300.synth import workload_large
     img = workload_large().image()[:256, 2816:3072].copy()
     op = ofit.make_plan(10.0, 255, K=16)
@@ -91,7 +90,7 @@ def test_bf16_compensated_on_small_denominators(B):
     for form, prec in (("fp16", B.FBF_FP16_TC), ("bf16", B.FBF_BF16_TC)):
         plan = B.Plan(10.0, 255, 10.0, K=16, precision=prec)
         errs[form] = float(np.abs(_run(B, plan, img) - ref).max())
-    assert errs["bf16"] <= 0.75, errs
+    assert errs["bf16"] <= TOL["bf16"], errs
     assert errs["bf16"] < 0.5 * errs["fp16"], errs
     assert B.fbf_device_errors() == 0
 
