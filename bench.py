@@ -182,10 +182,10 @@ def _traffic_for(kernel: str):
 def _tc_mma_flops(K: int, r: int, H: int, W: int, compensated: bool = False) -> float:
     """FP16-equivalent dense MMA flops one tensor-core launch executes (banded Toeplitz
     contractions, padding included; TF32 counts twice, at half the FP16 rate).  The
-    compensated BF16 form runs three x-pass products, a 32-row tile at r > 15, and an extra
-    FP16 y pass for the low part of the x-pass result."""
+    compensated BF16 form runs three x-pass products and an extra FP16 y pass for the low
+    part of the x-pass result."""
     R = 6 if r <= 6 else 15 if r <= 15 else 30
-    ty = 32 if (compensated and R > 15) else 64
+    ty = 64
     kx = (128 + 2 * R + 15) // 16 * 16
     ky = (ty + 2 * R + 15) // 16 * 16
     tiles = math.ceil(W / 128) * math.ceil(H / ty)

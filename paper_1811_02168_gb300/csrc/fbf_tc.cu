@@ -74,22 +74,24 @@ template <int RAD, int NPART>
 struct TcCfg {
   static constexpr int HX = TILE_X + 2 * RAD;             // halo columns
   static constexpr int KX = (HX + 15) / 16 * 16;          // x-pass K
-  // tile height: 64; 32 for the compensated form at r > 15, where the split x-pass result
-  // (below) needs the tensor-memory columns of a taller tile
-  static constexpr int TY = (NPART == 2 && RAD > 15) ? 32 : TILE_Y_MAX;
+  static constexpr int TY = TILE_Y_MAX;
+  // the compensated form at r > 15 keeps Gx in shared memory (the split x-pass result takes
+  // its tensor-memory columns); its x pass then reads both operands from shared memory
+  static constexpr bool GX_SMEM = NPART == 2 && RAD > 15;
   static constexpr int PX = TY / 4;                       // output pixels per compute thread
   static constexpr int HY = TY + 2 * RAD;                 // halo rows
   static constexpr int KY = (HY + 15) / 16 * 16;          // x-pass N = y-pass K
   static constexpr int GYB = TY * KY * 4;                 // Gy, TF32 (shared memory)
   static constexpr int GY16B = NPART == 2 ? TY * KY * 2 : 0;   // Gy, FP16: the lo part's y pass
   static constexpr int GLB = NPART == 2 ? TILE_X * KX * 2 : 0;   // Gx_lo (shared memory)
+  static constexpr int GXHB = GX_SMEM ? TILE_X * KX * 2 : 0;     // Gx (hi) in shared memory
   // B_h is produced as NC column chunks of CK x-pass K-steps (16 columns each) into a ring of
   // NSLOT chunk slots, each holding the chunk of both images of a pair (and of both parts of
   // the compensated form), with its own full / empty barriers: generation runs ahead of the
   // x pass by up to NSLOT chunks
   static constexpr int KS = KX / 16;
   static constexpr int CK = NPART == 1 ? (KS % 4 == 0 ? 4 : KS % 3 == 0 ? 3 : KS % 5 == 0 ? 5 : KS % 2 == 0 ? 2 : 1)
-                                       : (KS % 2 == 0 ? 2 : KS % 3 == 0 ? 3 : 1);
+                                       : GX_SMEM ? 1 : (KS % 2 == 0 ? 2 : KS % 3 == 0 ? 3 : 1);
   static constexpr int NC = KS / CK;
   static constexpr int CW = 16 * CK;                      // chunk columns
   static constexpr int CB = KY * CW * 2;                  // bytes of one image part's chunk (16-bit)
@@ -100,14 +102,14 @@ struct TcCfg {
   static constexpr int TABW = 2 * GENW + 512;             // words per term-table slot
   static constexpr int TABB = 2 * TABW * 4;               // 2 slots (terms k even / odd)
   static constexpr int BARB = 256;
-  static constexpr int FIXED = GYB + GY16B + GLB + FHB + TABB + BARB + 1024;
+  static constexpr int FIXED = GYB + GY16B + GLB + GXHB + FHB + TABB + BARB + 1024;
   static constexpr int NSLOT0 = (232448 - FIXED) / SLOTB;
   static constexpr int NSLOT = NSLOT0 < 2 * NC ? NSLOT0 : 2 * NC;
   static constexpr int SMEM = FIXED + NSLOT * SLOTB;
   // tensor memory: Gx (16-bit pairs, one column per two K elements), two x-pass and two
   // y-pass accumulators
   static constexpr int GXC = 0;
-  static constexpr int GXS = (KX / 2 + 31) / 32 * 32;
+  static constexpr int GXS = GX_SMEM ? 0 : (KX / 2 + 31) / 32 * 32;
   static constexpr int D1S = (KY + 31) / 32 * 32;
   static constexpr int D1C = GXS;
   // compensated form: the x-pass result splits into hi (TF32, in place) + lo (FP16 pairs,
@@ -507,8 +509,22 @@ __device__ __forceinline__ void load_taps(const DeviceParams& p, unsigned char* 
           make_uint4(pack2<T>(v[0], v[1]), pack2<T>(v[2], v[3]), pack2<T>(v[4], v[5]), pack2<T>(v[6], v[7]));
     }
   }
+  if (C::GX_SMEM) {
+    unsigned char* sGxh = sGl + C::GLB;
+    for (int i = tid; i < TILE_X * (C::KX / 8); i += NCT) {
+      const int o = i / (C::KX / 8), k8 = (i - o * (C::KX / 8)) * 8;
+      float v[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int d = k8 + j - o;
+        v[j] = (d >= 0 && d <= 2 * RAD) ? p.g[d] : 0.f;
+      }
+      *reinterpret_cast<uint4*>(sGxh + off16<C::KX>(o, k8)) =
+          make_uint4(pack2<T>(v[0], v[1]), pack2<T>(v[2], v[3]), pack2<T>(v[4], v[5]), pack2<T>(v[6], v[7]));
+    }
+  }
   const int warp = tid >> 5, lane = tid & 31;
-  if (warp < 4) {
+  if (warp < 4 && !C::GX_SMEM) {
     const int o = 32 * warp + lane;
     for (int j0 = 0; j0 < C::KX / 2; j0 += 8) {
       uint32_t v[8];
@@ -536,7 +552,7 @@ __device__ __forceinline__ void tc_body(const Src& src, const Scratch& sc) {
   unsigned char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   unsigned char* sGy = base;                        // y-pass B operand
   unsigned char* sGl = sGy + C::GYB + C::GY16B;     // Gx_lo (compensated form; Gy16 before it)
-  unsigned char* sBh = sGl + C::GLB;                // chunk ring of the x-pass B operands
+  unsigned char* sBh = sGl + C::GLB + C::GXHB;      // chunk ring (Gx hi before it when in smem)
   unsigned char* sFh = sBh + C::NSLOT * C::SLOTB;   // f of the halo tile (uint8)
   uint32_t* sTab = reinterpret_cast<uint32_t*>(sFh + C::FHB);   // 2 term-table slots
   uint64_t* bars = reinterpret_cast<uint64_t*>(sTab + 2 * C::TABW);
@@ -603,6 +619,7 @@ __device__ __forceinline__ void tc_body(const Src& src, const Scratch& sc) {
       const uint64_t dGy16 = op_desc(smem_u32(sGy + C::GYB), 16 * C::KY);
       const uint64_t dBh = op_desc(smem_u32(sBh), 16 * C::CW);
       const uint64_t dGl = op_desc(smem_u32(sGl), 16 * C::KX);
+      const uint64_t dGxh = op_desc(smem_u32(sGl + C::GLB), 16 * C::KX);
       uint32_t P = 0;
       int slot0 = 0, ring0 = 0;        // ring slot and use count of the next chunk
       bool ab = false;
@@ -629,12 +646,15 @@ __device__ __forceinline__ void tc_body(const Src& src, const Scratch& sc) {
               for (int kk = 0; kk < C::CK; ++kk) {
                 const int ks = c * C::CK + kk;
                 const uint64_t bhi = dBh + (uint64_t)((slot0 * C::SLOTB + s * C::CB + kk * 256) >> 4);
-                mma_ts_f16(tmem + C::D1C + s * C::D1S, tmem + C::GXC + 8 * ks, bhi, idX, ks > 0 ? 1u : 0u);
-                if (NPART == 2) {
-                  mma_ts_f16(tmem + C::D1C + s * C::D1S, tmem + C::GXC + 8 * ks,
-                             bhi + (uint64_t)((2 * C::CB) >> 4), idX, 1u);
-                  mma_ss_el(tmem + C::D1C + s * C::D1S, dGl + (uint64_t)(16 * ks), bhi, idX, 1u);
+                const uint64_t blo = bhi + (uint64_t)((2 * C::CB) >> 4);
+                if (C::GX_SMEM) {
+                  mma_ss_el(tmem + C::D1C + s * C::D1S, dGxh + (uint64_t)(16 * ks), bhi, idX, ks > 0 ? 1u : 0u);
+                  mma_ss_el(tmem + C::D1C + s * C::D1S, dGxh + (uint64_t)(16 * ks), blo, idX, 1u);
+                } else {
+                  mma_ts_f16(tmem + C::D1C + s * C::D1S, tmem + C::GXC + 8 * ks, bhi, idX, ks > 0 ? 1u : 0u);
+                  if (NPART == 2) mma_ts_f16(tmem + C::D1C + s * C::D1S, tmem + C::GXC + 8 * ks, blo, idX, 1u);
                 }
+                if (NPART == 2) mma_ss_el(tmem + C::D1C + s * C::D1S, dGl + (uint64_t)(16 * ks), bhi, idX, 1u);
               }
               if (c == C::NC - 1) mma_commit_el(s ? bXb : bXa);
             }
