@@ -13,6 +13,14 @@ constexpr int NXH = 8;                 // x outputs per lane in the x pass
 constexpr float kOutside = -3.0e38f;   // marks halo pixels outside the image
 constexpr int TABN = 256;              // per-term (cos, sin) table over integer intensities
 
+// largest divisor of rows_per_warp whose group keeps at most 24 loads per lane in flight
+__host__ __device__ constexpr int stage_group(int rows_per_warp, int cols_per_lane) {
+  int g = 24 / cols_per_lane;
+  if (g < 1) g = 1;
+  while (g > 1 && rows_per_warp % g != 0) --g;
+  return g;
+}
+
 template <int RAD, int TY, int NT, int NY>
 struct Cfg {
   static constexpr int NW = NT / 32;                       // warps
@@ -27,9 +35,14 @@ struct Cfg {
   static constexpr int HS2 = TX + 2;                       // x-pass buffer row stride (float2)
   static constexpr int CPS0 = HROWS_P * HS2;
   static constexpr int CPS = CPS0 + ((4 - CPS0 % 16) + 16) % 16;  // pair stride, == 4 (mod 16)
+  // f-halo staging: rows per warp, columns per lane, rows per group of loads in flight
+  static constexpr int STAGE_RPW = HROWS_P / NW;
+  static constexpr int STAGE_CPL = (TXH + 31) / 32;
+  static constexpr int STAGE_RG = stage_group(STAGE_RPW, STAGE_CPL);
   static constexpr size_t SMEM_BYTES =
       (size_t)(NW * STAGE_F2 + 2 * CPS + 2 * TABN) * 8 + (size_t)HROWS_P * FHS * 4 + 16;
   static_assert(TX * TY == NT * NY, "y-pass mapping: one column of NY pixels per thread");
+  static_assert(HROWS_P % NW == 0, "f-halo staging: whole rows per warp");
   static_assert(TY % NY == 0 && (TY / NY) * 32 == NT, "y-pass mapping");
   static_assert(SMEM_BYTES <= 232448, "shared memory per CTA exceeds 227 KB");
 };
@@ -230,19 +243,42 @@ __device__ __forceinline__ void fbf_body(const Src& src, const Scratch& sc) {
 
     // f of the tile plus halo (rows padded to whole x-pass rounds); kOutside marks
     // pixels outside the image.  The tile uses the term tables when all its values are
-    // integers in [0, min(R, TABN-1)] (8-bit images), else the sincospi path.
+    // integers in [0, min(R, TABN-1)] (8-bit images), else the sincospi path.  Each warp
+    // copies whole rows (coalesced); every load of a group of rows is issued before the
+    // first store, so a tile costs one or two memory round trips, not one per row.
     const float vmax = (float)min(p.R, TABN - 1);
     int ok = 1;
-#pragma unroll 4
-    for (int i = tid; i < C::HROWS_P * C::TXH; i += NT) {
-      const int row = i / C::TXH, xx = i - row * C::TXH;
-      const int gy = ty0 - RAD + row, gx = tx0 - RAD + xx;
-      float v = kOutside;
-      if (row < C::HROWS && gy >= 0 && gy < H && gx >= 0 && gx < W) {
-        v = __ldg(in + (long)gy * pitch + gx);
-        ok &= (v == rintf(v)) & (v >= 0.f) & (v <= vmax);
+    {
+      constexpr int CPL = C::STAGE_CPL, RPW = C::STAGE_RPW, RG = C::STAGE_RG;
+      for (int g0 = 0; g0 < RPW; g0 += RG) {
+        float v[RG][CPL];
+#pragma unroll
+        for (int a = 0; a < RG; ++a) {
+          const int row = (g0 + a) * C::NW + warp;
+          const int gy = ty0 - RAD + row;
+          const bool rin = row < C::HROWS && gy >= 0 && gy < H;
+          const float* __restrict__ src_row = in + (long long)(rin ? gy : 0) * pitch;
+#pragma unroll
+          for (int b = 0; b < CPL; ++b) {
+            const int xx = lane + 32 * b;
+            const int gx = tx0 - RAD + xx;
+            v[a][b] = (rin && xx < C::TXH && gx >= 0 && gx < W) ? __ldg(src_row + gx) : kOutside;
+          }
+        }
+#pragma unroll
+        for (int a = 0; a < RG; ++a) {
+          const int row = (g0 + a) * C::NW + warp;
+#pragma unroll
+          for (int b = 0; b < CPL; ++b) {
+            const int xx = lane + 32 * b;
+            if (xx < C::TXH) {
+              const float x = v[a][b];
+              if (x > kOutside) ok &= (x == rintf(x)) & (x >= 0.f) & (x <= vmax);
+              fh[row * C::FHS + xx] = x;
+            }
+          }
+        }
       }
-      fh[row * C::FHS + xx] = v;
     }
     // every halo pixel inside the image: generation needs no masking
     const bool interior = tx0 - RAD >= 0 && ty0 - RAD >= 0 && tx0 + TX + RAD <= W &&

@@ -148,8 +148,10 @@ class Server:
 
 
 class TorchBackend:
-    """Device backend on the library's batched path: inputs copied on a copy stream,
-    one batched launch per server launch on the compute stream, results copied back.
+    """Device backend on the library's batched path: inputs copied in on an upload stream as
+    soon as a request is admitted, one batched launch per server launch on the compute
+    stream, results copied back on a download stream.  Uploads never queue behind a
+    download (which waits for its launch to finish), so admission overlaps compute.
     ``precision`` selects the form every request is filtered in (FBF_FP32, FBF_FP16_TC,
     FBF_BF16_TC)."""
 
@@ -158,7 +160,8 @@ class TorchBackend:
         self.torch = torch
         self.B = binding
         self.dev = torch.device("cuda", device)
-        self.copy = torch.cuda.Stream(self.dev)
+        self.h2d = torch.cuda.Stream(self.dev)
+        self.d2h = torch.cuda.Stream(self.dev)
         self.compute = torch.cuda.Stream(self.dev)
         self.plans = {}
         self.precision = precision
@@ -172,12 +175,12 @@ class TorchBackend:
 
     def admit(self, r: Request):
         torch = self.torch
-        with torch.cuda.stream(self.copy):
+        with torch.cuda.stream(self.h2d):
             x = torch.empty((r.H, r.W), dtype=torch.float32, device=self.dev)
             y = torch.empty((r.H, r.W), dtype=torch.float32, device=self.dev)
             x.copy_(r.host_in, non_blocking=True)
             ev = torch.cuda.Event()
-            ev.record(self.copy)
+            ev.record(self.h2d)
         r.dev = (x, y, ev)
 
     def launch(self, rs: list[Request]):
@@ -191,12 +194,13 @@ class TorchBackend:
         self.batch.launch(self.compute)
         k_done = torch.cuda.Event()
         k_done.record(self.compute)
-        self.copy.wait_event(k_done)
-        with torch.cuda.stream(self.copy):
+        self.d2h.wait_event(k_done)
+        with torch.cuda.stream(self.d2h):
             for r in rs:
+                r.dev[1].record_stream(self.d2h)
                 r.host_out.copy_(r.dev[1], non_blocking=True)
             done = torch.cuda.Event()
-            done.record(self.copy)
+            done.record(self.d2h)
         return done
 
     def done(self, h) -> bool:
