@@ -13,6 +13,17 @@ constexpr int NXH = 8;                 // x outputs per lane in the x pass
 constexpr float kOutside = -3.0e38f;   // marks halo pixels outside the image
 constexpr int TABN = 256;              // per-term (cos, sin) table over integer intensities
 
+// Split-tile hand-off: every thread of the block has stored its partial sums and passed a
+// block barrier; one thread then adds the block's weight to the tile counter with a
+// GPU-scope acquire-release atomic.  Release (cumulative through the barrier) publishes the
+// whole block's partials; acquire makes every earlier contributor's partials visible to the
+// block once the following barrier is passed.  Returns the counter's previous value.
+__device__ __forceinline__ int counter_add_acq_rel(int* counter, int v) {
+  int old;
+  asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], %2;" : "=r"(old) : "l"(counter), "r"(v) : "memory");
+  return old;
+}
+
 // largest divisor of rows_per_warp whose group keeps at most 24 loads per lane in flight
 __host__ __device__ constexpr int stage_group(int rows_per_warp, int cols_per_lane) {
   int g = 24 / cols_per_lane;
@@ -435,16 +446,14 @@ __device__ __forceinline__ void fbf_body(const Src& src, const Scratch& sc) {
         pp[a * NT + tid] = num[a];
         pp[(NY + a) * NT + tid] = den[a];
       }
-      __threadfence();
       __syncthreads();
       if (tid == 0) {
-        const int prev = atomicAdd(sc.counter + wk.counter_base + t, wmine);
+        const int prev = counter_add_acq_rel(sc.counter + wk.counter_base + t, wmine);
         s_last = (prev + wmine == wk.wtile);
       }
       __syncthreads();
       finish = s_last != 0;
       if (finish) {
-        __threadfence();
         // sum the partials of all contributing CTAs in CTA (= term) order
         const long long g0 = wk.wstart + t * wk.wtile;
         const long long c0 = g0 * G / sc.wtot;

@@ -866,16 +866,14 @@ __device__ __forceinline__ void tc_body(const Src& src, const Scratch& sc) {
           pp[a * NCT + tid] = nm[a];
           pp[(PX + a) * NCT + tid] = dn[a];
         }
-        __threadfence();
         sync_compute();
         if (tid == 0) {
-          const int prev = atomicAdd(sc.counter + cw.counter_base + t, wmine);
+          const int prev = fp32::counter_add_acq_rel(sc.counter + cw.counter_base + t, wmine);
           *sFin = (prev + wmine == cw.wtile);
         }
         sync_compute();
         finish = *sFin != 0;
         if (finish) {
-          __threadfence();
           const long long g0 = cw.wstart + t * cw.wtile;
           const long long c0 = g0 * G / sc.wtot;
           const long long c1 = (g0 + term_start(K - 1)) * G / sc.wtot;
