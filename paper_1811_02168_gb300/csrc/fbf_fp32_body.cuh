@@ -133,6 +133,22 @@ __device__ __forceinline__ void locate(const Src& src, long long s, long long wt
   if (u >= w.tiles * w.K) { ++i; u = 0; }
 }
 
+// The partial-sum slot that CTA cc (of G, weighted range [ceil(cc wtot / G),
+// ceil((cc + 1) wtot / G))) wrote for tile t of image img: 0 when t is the first tile its
+// range reaches, 1 when t is its last, -1 when no unit of t starts in its range.  cc is one
+// of the CTAs whose range meets the tile's units (c0 <= cc <= c1 of the finisher).  The
+// tensor-core kernel's finisher evaluates it one contributor per lane.
+template <class Src>
+__device__ __forceinline__ int contributor_slot(const Src& src, long long cc, long long G, long long wtot,
+                                                int img, long long t, int K) {
+  int fi, gi;
+  long long fu, gu;
+  locate(src, ceil_div_ll(cc * wtot, G), wtot, fi, fu);
+  locate(src, ceil_div_ll((cc + 1) * wtot, G), wtot, gi, gu);
+  if (!(fi < gi || (fi == gi && fu < gu))) return -1;
+  return (fi == img && fu / K == t) ? 0 : 1;
+}
+
 // (cos, sin)(k nu v) for any v: reduce x = k v by the period (n = x - P rint(x/P) lies in
 // [-P/2, P/2]), then the accurate sincospi.  Used for tiles whose values are not all
 // integers in [0, min(R, TABN-1)].

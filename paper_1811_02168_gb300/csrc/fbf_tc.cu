@@ -879,18 +879,20 @@ __device__ __forceinline__ void tc_body(const Src& src, const Scratch& sc) {
           const long long c1 = (g0 + term_start(K - 1)) * G / sc.wtot;
 #pragma unroll
           for (int a = 0; a < PX; ++a) { nm[a] = 0.f; dn[a] = 0.f; }
-          for (long long cc = c0; cc <= c1; ++cc) {
-            int fi, gi;
-            long long fu, gu;
-            locate(src, ceil_div_ll(cc * sc.wtot, G), sc.wtot, fi, fu);
-            locate(src, ceil_div_ll((cc + 1) * sc.wtot, G), sc.wtot, gi, gu);
-            if (!(fi < gi || (fi == gi && fu < gu))) continue;
-            const int sl = (fi == img && fu / K == t) ? 0 : 1;
-            const float* qp = sc.partial + ((cc * 2 + sl) * 2) * PX * NCT;
+          // each lane finds the slot of one contributor (the divisions run side by side),
+          // then every thread adds the slots in CTA order
+          for (long long base = c0; base <= c1; base += 32) {
+            const int my_sl = base + lane <= c1 ? fp32::contributor_slot(src, base + lane, G, sc.wtot, img, t, K) : -1;
+            const int n = (int)min(32LL, c1 - base + 1);
+            for (int q = 0; q < n; ++q) {
+              const int sl = __shfl_sync(0xffffffffu, my_sl, q);
+              if (sl < 0) continue;
+              const float* qp = sc.partial + (((base + q) * 2 + sl) * 2) * PX * NCT;
 #pragma unroll
-            for (int a = 0; a < PX; ++a) {
-              nm[a] += __ldcg(qp + a * NCT + tid);
-              dn[a] += __ldcg(qp + (PX + a) * NCT + tid);
+              for (int a = 0; a < PX; ++a) {
+                nm[a] += __ldcg(qp + a * NCT + tid);
+                dn[a] += __ldcg(qp + (PX + a) * NCT + tid);
+              }
             }
           }
           if (tid == 0) sc.counter[cw.counter_base + t] = 0;
