@@ -745,7 +745,7 @@ def run_batch(a):
 
 
 def run_serve(a):
-    """Poisson request stream (config 4 shape: 500 req/s, sides log-uniform in [512, 4096],
+    """Poisson request stream (500 req/s, sides log-uniform in [512, 4096],
     theta {2,5,10}, sigma {10,30,80}, K {4,8,16}) served with continuous batching under a
     40 GB HBM budget, and the same stream served one request per launch.  Request images are
     H x W windows (flat slices) of two pre-generated 4096 x 4096 mosaics in pinned memory;
@@ -783,7 +783,7 @@ def run_serve(a):
             out.append(r)
         return out
 
-    # config 4: the BF16-stack form (compensated BF16 tensor-core kernel) served with continuous
+    # the served form: the BF16 stack (compensated BF16 tensor-core kernel) with continuous
     # batching, against the plain FP32 form one request per launch; and FP32 with batching
     modes = (("continuous_batching", B.FBF_BF16_TC, True), ("one_at_a_time_fp32", B.FBF_FP32, False),
              ("continuous_batching_fp32", B.FBF_FP32, True))

@@ -17,7 +17,7 @@ TEST INFRASTRUCTURE ONLY -- see the package docstring.  Parity pins: tests/test_
                       images).
   * psnr           -- 10 log10(255^2 / MSE) (Section III).
 
-Readings (listed in the design doc): neighbours outside the image are absent from both sums of
+Readings where the paper is silent: neighbours outside the image are absent from both sums of
 eq. (1), which is zero padding of every channel including the constant one; a pixel whose
 denominator is <= 0 keeps its input value.
 """

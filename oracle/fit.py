@@ -11,7 +11,7 @@ Notation follows Section II of the paper:
   * e(K) = min_{T in N} E(K,T)                               eq. (6)
   * Algorithm 1: smallest K with e(K) <= eps, and its T.
 
-Readings where the paper is silent (each listed in the design doc):
+Readings where the paper is silent:
   * T_max is only "large" (Section II, text after Prop. 2): T_max = 4R; if the optimum sits
     above T_max/2 the scan is repeated with T_max doubled.
   * Round-off ties: for large K, E(K,T) reaches FP64 round-off for many T and the argmin

@@ -1,8 +1,8 @@
 """Served requests on the GPU: each result equals the same request filtered alone by
 fbf_filter, within the FP32 tolerance, although it was batched with whatever else had
 arrived (continuous batching) and its copies overlapped other launches.  Both the FP32 form
-and the compensated BF16 tensor-core form (config 4's served form): only the order of
-split-tile partial sums can differ between a batched and a lone launch."""
+and the compensated BF16 tensor-core form (the form the Poisson-stream bench serves): only
+the order of split-tile partial sums can differ between a batched and a lone launch."""
 import numpy as np
 import pytest
 
