@@ -43,6 +43,8 @@ def _args():
     ap.add_argument("--serve-seconds", type=float, default=10.0,
                     help="length of the Poisson request stream for --workload serve")
     ap.add_argument("--serve-rate", type=float, default=500.0)
+    ap.add_argument("--serve-idle-sleep", type=float, default=5e-5,
+                    help="seconds the serving loop sleeps when it has nothing to do (0: poll)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-rows", type=int, default=96, help="oracle sample: rows per sigma")
     return ap.parse_args()
@@ -803,7 +805,8 @@ def run_serve(a):
     for mode, prec, batching in modes:
         reqs = make_requests()
         torch.cuda.synchronize(dev)
-        st = Server(backends[prec], 40 << 30, max_batch=256, max_inflight=2, batching=batching).run(reqs)
+        st = Server(backends[prec], 40 << 30, max_batch=256, max_inflight=2, batching=batching).run(
+            reqs, idle_sleep=a.serve_idle_sleep)
         results[mode] = st.summary()
     clk = clocks.stop()
     cb = results["continuous_batching"]

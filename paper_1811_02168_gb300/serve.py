@@ -37,6 +37,7 @@ class Request:
     host_in: object = None    # host image (backend specific)
     host_out: object = None
     admitted: float = math.nan
+    launched: float = math.nan
     done: float = math.nan
     dev: object = None        # backend state
 
@@ -55,6 +56,9 @@ class ServeStats:
     pixels: int = 0
     wall_s: float = 0.0
     latencies: list = field(default_factory=list)
+    # per served request: (latency, arrival -> admitted, admitted -> launched,
+    # launched -> result on the host, pixels, requests in its launch)
+    trace: list = field(default_factory=list)
     launches: int = 0
     max_inflight_seen: int = 0
     hbm_high_water: int = 0
@@ -73,7 +77,22 @@ class ServeStats:
                 "p50_ms": 1e3 * self.pct(50), "p99_ms": 1e3 * self.pct(99),
                 "launches": self.launches, "max_inflight": self.max_inflight_seen,
                 "hbm_high_water_bytes": self.hbm_high_water,
-                "waited_for_budget": self.waited_for_budget}
+                "waited_for_budget": self.waited_for_budget,
+                "slowest_1pct": self.tail_breakdown(99)}
+
+    def tail_breakdown(self, q: float) -> dict:
+        """Mean parts of the latency of the requests at or above the q-th percentile."""
+        if not self.trace:
+            return {}
+        cut = self.pct(q)
+        tail = [t for t in self.trace if t[0] >= cut]
+        n = len(tail)
+        return {"requests": n,
+                "queued_ms": 1e3 * sum(t[1] for t in tail) / n,
+                "wait_for_launch_ms": 1e3 * sum(t[2] for t in tail) / n,
+                "launch_to_result_ms": 1e3 * sum(t[3] for t in tail) / n,
+                "mpix": sum(t[4] for t in tail) / n / 1e6,
+                "batch_requests": sum(t[5] for t in tail) / n}
 
 
 class Server:
@@ -118,6 +137,8 @@ class Server:
                 busy = True
             # continuous batching: launch what is admitted whenever a launch slot is free
             if admitted and len(inflight) < self.max_inflight:
+                for r in admitted:
+                    r.launched = now
                 h = self.be.launch(admitted)
                 inflight.append((h, admitted))
                 st.launches += 1
@@ -132,6 +153,8 @@ class Server:
                     for r in rs:
                         r.done = t
                         st.latencies.append(r.latency)
+                        st.trace.append((r.latency, r.admitted - r.arrival, r.launched - r.admitted,
+                                         t - r.launched, r.H * r.W, len(rs)))
                         st.requests += 1
                         st.pixels += r.H * r.W
                         used -= r.nbytes
