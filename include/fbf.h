@@ -265,10 +265,12 @@ int fbf_lut_destroy(fbf_lut_t lut);
 
 const char* fbf_last_error(void);
 
-/* fbf_device_errors -- synchronise nothing; read (and with clear != 0 reset) the device
- * error word of the tensor-core kernels: bit 0 set means a bounded wait inside a kernel
- * gave up and that launch's output is incomplete.  Read it after synchronising the
- * stream of the launches in question. */
+/* fbf_device_errors -- read (and with clear != 0 reset) the device error word of the
+ * kernels: bit 0 set means a bounded mbarrier wait of a tensor-core kernel gave up, bit 1
+ * that a bounded wait for a TMA copy of the f halo in the FP32 kernel gave up; in either
+ * case that launch's output is incomplete.  Read it after synchronising the stream of the
+ * launches in question.  Clearing a nonzero word also resets the library's cached
+ * split-tile counters (synchronising the devices that hold them). */
 int fbf_device_errors(int* flags, int clear);
 
 /* fbf_version -- library version string. */

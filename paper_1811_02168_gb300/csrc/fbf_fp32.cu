@@ -23,13 +23,19 @@
 // slot and adds its weight to the tile's counter; the last one sums the partials in CTA
 // order (ascending k, independent of timing) and divides.
 //
-// Per tile a CTA stages f of the tile plus an r-pixel halo in shared memory.  Per term,
+// Per tile a CTA stages f of the tile plus an r-pixel halo in shared memory: for single
+// images at r <= 15 whose base and row stride are 16-byte aligned, by TMA (a 2-D tensor map
+// of the image; the next tile's box is loaded into a second buffer while the current tile is
+// filtered; elements outside the image arrive as NaN, which marks them as absent), otherwise
+// by plain loads (whole rows per warp; outside pixels marked by a sentinel).  Per term,
 //   1. each warp, four halo rows at a time, generates the term's image pairs into a
 //      warp-private buffer and convolves them along x (8 outputs per lane) into a shared
 //      buffer of TY + 2r rows; only __syncwarp separates the two;
 //   2. after one CTA barrier each thread convolves that buffer along y for its own pixels
 //      and folds the results into its num/den registers.
 // Only f is read from and only f_BF (and split-tile partials) written to global memory.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -90,9 +96,76 @@ int get_workspace(int dev, cudaStream_t st, size_t partial_bytes, size_t counter
 }
 
 
+// Zero the tile counters of every cached workspace (after a launch that gave up part way
+// left some of them nonzero).  Synchronises each device that has a workspace.
+int reset_workspace_counters() {
+  std::lock_guard<std::mutex> lk(g_ws_mu);
+  int cur = 0;
+  cudaGetDevice(&cur);
+  for (auto& kv : g_ws) {
+    Workspace& w = kv.second;
+    if (!w.base) continue;
+    cudaSetDevice(kv.first.first);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemset(w.base, 0, align256(w.counter_cap * sizeof(int)));
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+      cudaSetDevice(cur);
+      return set_error(FBF_ECUDA, std::string("fbf_device_errors: ") + cudaGetErrorString(e));
+    }
+  }
+  cudaSetDevice(cur);
+  return FBF_OK;
+}
+
+// The FP32 device error word of this translation unit's kernels (the single-image ones).
+int fp32_device_errors(int* flags, int clear) {
+  int v = 0;
+  cudaError_t e = cudaMemcpyFromSymbol(&v, fp32::g_fp32_error, sizeof(int));
+  if (e != cudaSuccess) return set_error(FBF_ECUDA, std::string("fbf_device_errors: ") + cudaGetErrorString(e));
+  if (clear && v) {
+    const int z = 0;
+    e = cudaMemcpyToSymbol(fp32::g_fp32_error, &z, sizeof(int));
+    if (e != cudaSuccess) return set_error(FBF_ECUDA, std::string("fbf_device_errors: ") + cudaGetErrorString(e));
+  }
+  *flags = v;
+  return FBF_OK;
+}
+
 namespace {
 
 using namespace fp32;
+
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime (no link
+// dependence on the driver library)
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      f = nullptr;
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  }();
+  return fn;
+}
+
+// Tensor map of the image for the TMA staging of the f halo: FP32, dims {W, H}, row stride
+// pitch, box {box_w, box_h}, NaN for elements outside the image.  False when the image does
+// not allow one (base not 16-byte aligned, row stride not a multiple of 16 bytes) or the
+// driver has no encoder; the caller then stages with plain loads.
+bool encode_f_map(CUtensorMap* map, const float* in, int H, int W, size_t pitch, int box_w, int box_h) {
+  if ((reinterpret_cast<uintptr_t>(in) & 15) != 0 || (pitch * sizeof(float)) % 16 != 0) return false;
+  const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)W, (cuuint64_t)H};
+  const cuuint64_t strides[1] = {(cuuint64_t)(pitch * sizeof(float))};
+  const cuuint32_t box[2] = {(cuuint32_t)box_w, (cuuint32_t)box_h};
+  const cuuint32_t estr[2] = {1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(in), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NAN_REQUEST_ZERO_FMA) == CUDA_SUCCESS;
+}
 
 // SMs and resident CTAs of one instantiation on one device (set once per device)
 template <class KernelFn>
@@ -143,8 +216,21 @@ int launch_cfg(const DeviceParams& dp, const float* in, float* out, int H, int W
   if (e != cudaSuccess) return set_error(FBF_ECUDA, std::string("fbf_filter: ") + cudaGetErrorString(e));
   if (dev < 0 || dev >= 64) return set_error(FBF_EUNSUPPORTED, "fbf_filter: device index >= 64");
   int nsm = 0, nocc = 0;
-  int rc = kernel_slots(fbf_fp32_kernel<RAD, TY, NT, NY>, NT, C::SMEM_BYTES, dev, &nsm, &nocc, sms, occ,
-                        "fbf_filter");
+  int rc = FBF_OK;
+  CUtensorMap map;
+  bool tma = false;
+  if constexpr (C::TMA_OK) {
+    tma = encode_f_map(&map, in, H, W, pitch, C::TMA_BW, C::HROWS_P);
+    if (tma) {
+      static int occ_t[64] = {0};
+      static int sms_t[64] = {0};
+      rc = kernel_slots(fbf_fp32_tma_kernel<RAD, TY, NT, NY>, NT, C::TMA_SMEM_BYTES, dev, &nsm, &nocc, sms_t,
+                        occ_t, "fbf_filter");
+    }
+  }
+  if (!tma)
+    rc = kernel_slots(fbf_fp32_kernel<RAD, TY, NT, NY>, NT, C::SMEM_BYTES, dev, &nsm, &nocc, sms, occ,
+                      "fbf_filter");
   if (rc != FBF_OK) return rc;
   const DeviceParams p = pad_params<RAD>(dp);
   const Work w = single_work(in, out, H, W, pitch, dp.K, TY);
@@ -156,7 +242,14 @@ int launch_cfg(const DeviceParams& dp, const float* in, float* out, int H, int W
   const size_t partial_bytes = (size_t)G * 2 * 2 * NY * NT * sizeof(float);
   rc = get_workspace(dev, st, partial_bytes, (size_t)w.tiles, &sc.partial, &sc.counter);
   if (rc != FBF_OK) return rc;
-  fbf_fp32_kernel<RAD, TY, NT, NY><<<(unsigned)G, NT, C::SMEM_BYTES, st>>>(p, w, sc);
+  bool launched = false;
+  if constexpr (C::TMA_OK) {
+    if (tma) {
+      fbf_fp32_tma_kernel<RAD, TY, NT, NY><<<(unsigned)G, NT, C::TMA_SMEM_BYTES, st>>>(p, w, sc, map);
+      launched = true;
+    }
+  }
+  if (!launched) fbf_fp32_kernel<RAD, TY, NT, NY><<<(unsigned)G, NT, C::SMEM_BYTES, st>>>(p, w, sc);
   e = cudaGetLastError();
   if (e != cudaSuccess) return set_error(FBF_ECUDA, std::string("fbf_filter: launch: ") + cudaGetErrorString(e));
   return FBF_OK;

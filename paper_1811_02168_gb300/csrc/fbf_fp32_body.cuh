@@ -1,6 +1,7 @@
 // Shared by the single-image and batched launchers: the FP32 fused Fourier bilateral
 // filter kernel body (see fbf_fp32.cu for the description of the method and schedule).
 #pragma once
+#include <cuda.h>   // CUtensorMap (the type only; maps are encoded on the host)
 #include <cuda_runtime.h>
 
 #include "fbf_internal.h"
@@ -23,6 +24,53 @@ __device__ __forceinline__ int counter_add_acq_rel(int* counter, int v) {
   asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], %2;" : "=r"(old) : "l"(counter), "r"(v) : "memory");
   return old;
 }
+
+// ---- TMA helpers (f-halo staging) ----------------------------------------------------------
+// Bounded wait: each poll may suspend the thread for up to kTmaSuspendNs (woken early when the
+// phase completes); gives up (false) after kTmaWaitLimit polls or kTmaWaitNs of wall time.
+constexpr uint32_t kTmaSuspendNs = 1000000;
+constexpr unsigned long long kTmaWaitNs = 2000000000ull;
+constexpr int kTmaWaitLimit = 1 << 22;
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void tma_bar_init(unsigned long long* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_addr(bar)) : "memory");
+}
+// Load the box at (x, y) of `map` into dst and have it complete phase of `bar` (bytes = box size,
+// elements outside the image included: they arrive as NaN).
+__device__ __forceinline__ void tma_load_box(float* dst, const CUtensorMap* map, int x, int y,
+                                             unsigned long long* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+               :: "r"(smem_addr(bar)), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+               " [%0], [%1, {%2, %3}], [%4];"
+               :: "r"(smem_addr(dst)), "l"(map), "r"(x), "r"(y), "r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ bool tma_bar_wait(unsigned long long* bar, uint32_t parity) {
+  const uint32_t a = smem_addr(bar);
+  unsigned long long t0 = 0;
+  for (int it = 0; it < kTmaWaitLimit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done) : "r"(a), "r"(parity), "r"(kTmaSuspendNs) : "memory");
+    if (done) return true;
+    if ((it & 15) == 0) {
+      unsigned long long now;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
+      if (it == 0) t0 = now;
+      else if (now - t0 > kTmaWaitNs) return false;
+    }
+  }
+  return false;
+}
+
+// Device error word of the FP32 kernels (bit 1: a TMA wait gave up; that launch's output is
+// incomplete).  Each translation unit has its own copy; the single-image launcher reads its own.
+static __device__ int g_fp32_error;
 
 // largest divisor of rows_per_warp whose group keeps at most 24 loads per lane in flight
 __host__ __device__ constexpr int stage_group(int rows_per_warp, int cols_per_lane) {
@@ -52,6 +100,16 @@ struct Cfg {
   static constexpr int STAGE_RG = stage_group(STAGE_RPW, STAGE_CPL);
   static constexpr size_t SMEM_BYTES =
       (size_t)(NW * STAGE_F2 + 2 * CPS + 2 * TABN) * 8 + (size_t)HROWS_P * FHS * 4 + 16;
+  // TMA staging of the f halo (single-image launches): a box of TMA_BW x HROWS_P floats whose
+  // first column, tx0 - TMA_RX, is 16-byte aligned (tx0 is a multiple of 32); two buffers
+  // (the next tile's box is loaded during the current tile), 128-byte aligned.
+  static constexpr int TMA_RX = (RAD + 3) / 4 * 4;
+  static constexpr int TMA_OFF = TMA_RX - RAD;                     // halo column 0 in the box
+  static constexpr int TMA_BW = (TXH + TMA_OFF + 3) / 4 * 4;       // box width = row stride
+  static constexpr int TMA_FH = HROWS_P * TMA_BW;                  // floats per buffer
+  static constexpr size_t TMA_SMEM_BYTES =
+      128 + (size_t)2 * TMA_FH * 4 + (size_t)(NW * STAGE_F2 + 2 * CPS + 2 * TABN) * 8 + 16;
+  static constexpr bool TMA_OK = RAD <= 15 && TMA_BW <= 256 && HROWS_P <= 256 && TMA_SMEM_BYTES <= 232448;
   static_assert(TX * TY == NT * NY, "y-pass mapping: one column of NY pixels per thread");
   static_assert(HROWS_P % NW == 0, "f-halo staging: whole rows per warp");
   static_assert(TY % NY == 0 && (TY / NY) * 32 == NT, "y-pass mapping");
@@ -80,6 +138,7 @@ struct Scratch {
 
 // A single image whose parameters sit in the constant bank (kernel parameter).
 struct SingleSrc {
+  static constexpr bool kTma = false;
   const DeviceParams* p;
   Work w;
   __device__ __forceinline__ int count() const { return 1; }
@@ -88,8 +147,23 @@ struct SingleSrc {
   __device__ __forceinline__ int find(long long) const { return 0; }
 };
 
+// A single image whose f halo tiles are fetched by TMA through `map` (a kernel parameter
+// encoded on the host: FP32, dims {W, H}, row stride pitch, box {TMA_BW, HROWS_P}, NaN for
+// elements outside the image).
+struct SingleSrcTma {
+  static constexpr bool kTma = true;
+  const DeviceParams* p;
+  Work w;
+  const CUtensorMap* map;
+  __device__ __forceinline__ int count() const { return 1; }
+  __device__ __forceinline__ Work work(int) const { return w; }
+  __device__ __forceinline__ const DeviceParams& params(int) const { return *p; }
+  __device__ __forceinline__ int find(long long) const { return 0; }
+};
+
 // A device work-list of images (batched launch).
 struct ListSrc {
+  static constexpr bool kTma = false;
   const DeviceParams* __restrict__ prm;
   const Work* __restrict__ wl;
   int n;
@@ -221,15 +295,24 @@ __device__ __forceinline__ void xconv8(const float2* __restrict__ srow, const De
 template <int RAD, int TY, int NT, int NY, class Src>
 __device__ __forceinline__ void fbf_body(const Src& src, const Scratch& sc) {
   using C = Cfg<RAD, TY, NT, NY>;
+  constexpr bool TMA = Src::kTma;
+  static_assert(!TMA || C::TMA_OK, "TMA staging does not fit this configuration");
+  constexpr int FS = TMA ? C::TMA_BW : C::FHS;        // f-halo row stride (floats)
   extern __shared__ float4 smem_f4[];
-  float2* smem2 = reinterpret_cast<float2*>(smem_f4);
+  // TMA: two f buffers first (128-byte aligned), then the plain path's layout without its f.
+  // The alignment is a byte offset added to the shared array itself, so every pointer below
+  // stays a known shared-memory pointer (shared loads and stores, not generic ones).
+  float* fhb = reinterpret_cast<float*>(reinterpret_cast<char*>(smem_f4) +
+                                        ((128u - (smem_addr(smem_f4) & 127u)) & 127u));
+  float2* smem2 = TMA ? reinterpret_cast<float2*>(fhb + 2 * C::TMA_FH) : reinterpret_cast<float2*>(smem_f4);
   const int tid = threadIdx.x;
   const int lane = tid & 31;
   const int warp = tid >> 5;
   float2* stage = smem2 + warp * C::STAGE_F2;
   float2* hbuf = smem2 + C::NW * C::STAGE_F2;
   float2* tabs = hbuf + 2 * C::CPS;                    // two term tables (double buffer)
-  float* fh = reinterpret_cast<float*>(tabs + 2 * TABN);
+  float* fh = reinterpret_cast<float*>(tabs + 2 * TABN);     // TMA: set per tile
+  unsigned long long* fbar = reinterpret_cast<unsigned long long*>(tabs + 2 * TABN);   // TMA
   __shared__ int s_last;
 
   const int G = gridDim.x;
@@ -242,6 +325,25 @@ __device__ __forceinline__ void fbf_body(const Src& src, const Scratch& sc) {
   locate(src, Lc1, sc.wtot, img_end, u_end);
   img_first = img;
   u_first = u;
+
+  // TMA: one mbarrier per f buffer; the first tile's box is requested at once, each later
+  // one while the tile before it is filtered
+  uint32_t fph = 0;   // phase parity to wait for, per buffer
+  int fb = 0;         // buffer of the current tile
+  if constexpr (TMA) {
+    if (tid == 0) {
+      tma_bar_init(fbar);
+      tma_bar_init(fbar + 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (tid == 0 && (img < img_end || (img == img_end && u < u_end))) {
+      const Work w0 = src.work(img);
+      const long long t0 = u / w0.K;
+      tma_load_box(fhb, src.map, (int)(t0 % w0.tiles_x) * TX - C::TMA_RX, (int)(t0 / w0.tiles_x) * TY - RAD,
+                   fbar, C::TMA_FH * 4);
+    }
+  }
 
   // own pixels: one column of NY rows
   const int ox = lane;
@@ -275,7 +377,28 @@ __device__ __forceinline__ void fbf_body(const Src& src, const Scratch& sc) {
     // first store, so a tile costs one or two memory round trips, not one per row.
     const float vmax = (float)min(p.R, TABN - 1);
     int ok = 1;
-    {
+    if constexpr (TMA) {
+      // this tile's box was requested by the previous tile (or above); NaN marks outside pixels
+      const uint32_t par = (fph >> fb) & 1u;
+      const bool got = tma_bar_wait(fbar + fb, par);
+      fph ^= 1u << fb;
+      if (__syncthreads_or(!got)) {
+        // gave up: record it, let the copy in flight land (bounded), and leave
+        if (tid == 0) {
+          atomicOr(&g_fp32_error, 2);
+          tma_bar_wait(fbar + fb, par);
+        }
+        return;
+      }
+      fh = fhb + fb * C::TMA_FH + C::TMA_OFF;
+      for (int row = warp; row < C::HROWS; row += C::NW) {
+#pragma unroll
+        for (int xx = lane; xx < C::TXH; xx += 32) {
+          const float x = fh[row * FS + xx];
+          if (x > kOutside) ok &= (x == rintf(x)) & (x >= 0.f) & (x <= vmax);
+        }
+      }
+    } else {
       constexpr int CPL = C::STAGE_CPL, RPW = C::STAGE_RPW, RG = C::STAGE_RG;
       for (int g0 = 0; g0 < RPW; g0 += RG) {
         float v[RG][CPL];
@@ -311,6 +434,18 @@ __device__ __forceinline__ void fbf_body(const Src& src, const Scratch& sc) {
     const bool interior = tx0 - RAD >= 0 && ty0 - RAD >= 0 && tx0 + TX + RAD <= W &&
                           ty0 + TY + RAD <= H;
     const bool tile_int = __syncthreads_and(ok) != 0;
+    if constexpr (TMA) {
+      // request the next tile's box into the other buffer, last read by the previous tile
+      // (before the barrier that closed it)
+      const long long un = t * K + ke;
+      if (tid == 0 && un < wk.tiles * K && (img < img_end || un < u_end)) {
+        const long long tn = un / K;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        tma_load_box(fhb + (fb ^ 1) * C::TMA_FH, src.map, (int)(tn % wk.tiles_x) * TX - C::TMA_RX,
+                     (int)(tn / wk.tiles_x) * TY - RAD, fbar + (fb ^ 1), C::TMA_FH * 4);
+      }
+      fb ^= 1;
+    }
     if (tile_int && kb >= 1) {
       build_term_table<NT>(p, kb, tabs + (kb & 1) * TABN);
       __syncthreads();
@@ -332,7 +467,7 @@ __device__ __forceinline__ void fbf_body(const Src& src, const Scratch& sc) {
           for (int r8 = 0; r8 < 8; ++r8) {
 #pragma unroll
             for (int xx = lane; xx < C::TXH; xx += 32) {
-              const float v = fh[(rb + r8) * C::FHS + xx];
+              const float v = fh[(rb + r8) * FS + xx];
               stage[r8 * C::SWP + xx] = (v > kOutside) ? make_float2(v - m, 1.f) : make_float2(0.f, 0.f);
             }
           }
@@ -350,7 +485,7 @@ __device__ __forceinline__ void fbf_body(const Src& src, const Scratch& sc) {
             for (int r4 = 0; r4 < 4; ++r4) {
 #pragma unroll
               for (int xx = lane; xx < C::TXH; xx += 32) {
-                const float v = fh[(rb + r4) * C::FHS + xx];
+                const float v = fh[(rb + r4) * FS + xx];
                 const float2 cs = tab_lookup(tab, v);
                 const float fm = v - m;
                 stage[(r4 * 2) * C::SWP + xx] = cs;
@@ -362,7 +497,7 @@ __device__ __forceinline__ void fbf_body(const Src& src, const Scratch& sc) {
             for (int r4 = 0; r4 < 4; ++r4) {
 #pragma unroll
               for (int xx = lane; xx < C::TXH; xx += 32) {
-                const float v = fh[(rb + r4) * C::FHS + xx];
+                const float v = fh[(rb + r4) * FS + xx];
                 const bool in_img = v > kOutside;
                 float2 cs = tab_lookup(tab, in_img ? v : 0.f);
                 cs.x = in_img ? cs.x : 0.f;
@@ -377,7 +512,7 @@ __device__ __forceinline__ void fbf_body(const Src& src, const Scratch& sc) {
             for (int r4 = 0; r4 < 4; ++r4) {
 #pragma unroll
               for (int xx = lane; xx < C::TXH; xx += 32) {
-                const float v = fh[(rb + r4) * C::FHS + xx];
+                const float v = fh[(rb + r4) * FS + xx];
                 const bool in_img = v > kOutside;
                 float2 cs = term_cs_any(kf, in_img ? v : 0.f, p);
                 cs.x = in_img ? cs.x : 0.f;
@@ -406,7 +541,7 @@ __device__ __forceinline__ void fbf_body(const Src& src, const Scratch& sc) {
         const float2* tab = tabs + (k & 1) * TABN;
 #pragma unroll
         for (int a = 0; a < NY; ++a) {
-          const float v = fh[(oy + a + RAD) * C::FHS + ox + RAD];
+          const float v = fh[(oy + a + RAD) * FS + ox + RAD];
           const bool in_img = v > kOutside;   // false only for pixels past the image edge
           const float2 cs = tile_int ? tab_lookup(tab, in_img ? v : 0.f) : term_cs_any(kf, v, p);
           w[a] = make_float2(ck * cs.x, ck * cs.y);
@@ -499,7 +634,7 @@ __device__ __forceinline__ void fbf_body(const Src& src, const Scratch& sc) {
         const int gy = ty0 + oy + a, gx = tx0 + ox;
         if (gy < H && gx < W) {
           const float d = den[a];
-          const float f = fh[(oy + a + RAD) * C::FHS + ox + RAD];
+          const float f = fh[(oy + a + RAD) * FS + ox + RAD];
           out[(long)gy * pitch + gx] = (d > 0.f) ? m + num[a] / d : f;
         }
       }
@@ -515,6 +650,15 @@ template <int RAD, int TY, int NT, int NY>
 __global__ void __launch_bounds__(NT, 1)
 fbf_fp32_kernel(const __grid_constant__ DeviceParams p, const Work w, const Scratch sc) {
   const SingleSrc src{&p, w};
+  fbf_body<RAD, TY, NT, NY>(src, sc);
+}
+
+// One image, parameters in the constant bank, f-halo tiles by TMA through `map`.
+template <int RAD, int TY, int NT, int NY>
+__global__ void __launch_bounds__(NT, 1)
+fbf_fp32_tma_kernel(const __grid_constant__ DeviceParams p, const Work w, const Scratch sc,
+                    const __grid_constant__ CUtensorMap map) {
+  const SingleSrcTma src{&p, w, &map};
   fbf_body<RAD, TY, NT, NY>(src, sc);
 }
 

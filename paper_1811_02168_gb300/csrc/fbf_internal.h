@@ -85,6 +85,10 @@ int launch_tc(const DeviceParams& dp, const float* in, float* out, int H, int W,
               void* stream, int precision);
 // Device error word of the tensor-core kernels (bit 0: a bounded wait gave up).
 int device_errors(int* flags, int clear);
+// FP32 single-image kernels' error word (bit 1: a TMA wait gave up), and the reset of the
+// cached split-tile counters that a launch which gave up part way leaves nonzero.
+int fp32_device_errors(int* flags, int clear);
+int reset_workspace_counters();
 
 // batched tensor-core launch of one radius class (6, 15 or 30) from a device work-list
 namespace fp32 { struct Work; }

@@ -1086,6 +1086,15 @@ int device_errors(int* flags, int clear) {
     e = cudaMemcpyToSymbol(tc::g_tc_error, &z, sizeof(int));
     if (e != cudaSuccess) return set_error(FBF_ECUDA, std::string("fbf_device_errors: ") + cudaGetErrorString(e));
   }
+  int v32 = 0;
+  int rc = fp32_device_errors(&v32, clear);
+  if (rc != FBF_OK) return rc;
+  v |= v32;
+  // a launch that gave up left some split-tile counters nonzero: clear them for the next one
+  if (clear && v) {
+    rc = reset_workspace_counters();
+    if (rc != FBF_OK) return rc;
+  }
   *flags = v;
   return FBF_OK;
 }
