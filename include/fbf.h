@@ -218,6 +218,78 @@ int fbf_batch_pending(fbf_batch_t batch, int* n);
 /* fbf_batch_destroy -- wait for the batch's launches, release its buffers (NULL ok). */
 int fbf_batch_destroy(fbf_batch_t batch);
 
+/* ---- serving: continuous batching under an HBM budget --------------------------------
+ * Not in the paper (Section III filters one image at a time); the arithmetic per request is
+ * exactly fbf_filter's.  A server owns a worker thread, three streams (upload, compute,
+ * download), a stream-ordered device memory pool and a batch.  Requests are admitted in
+ * arrival order while their device buffers (input and output, 8 bytes per pixel) fit the
+ * HBM budget and the next launch has room (max_batch); the image is copied in at once; all
+ * admitted requests go into one batched launch whenever fewer than max_inflight launches
+ * are in flight (requests that arrive meanwhile join the next launch); results are copied
+ * back on the download stream and the device buffers released.  Latency is measured from
+ * fbf_server_submit to the result being on the host.
+ */
+typedef struct fbf_server_s* fbf_server_t;
+
+typedef struct {
+  uint64_t requests;          /* finished with their result on the host                 */
+  uint64_t pixels;            /* their pixels                                           */
+  uint64_t launches;          /* batched launches                                       */
+  uint64_t failed;            /* requests that ended with an error                      */
+  uint64_t hbm_high_water;    /* most device bytes held by admitted requests at once    */
+  uint64_t waited_for_budget; /* requests whose admission the budget deferred           */
+  uint32_t max_inflight_seen; /* most launches in flight at once                        */
+  double wall_s;              /* first submit to last completion                        */
+  double p50_ms, p99_ms;      /* latency percentiles                                    */
+  double tail_requests;       /* requests at or above p99, and the means of their parts: */
+  double tail_queued_ms;      /*   submit -> admitted                                   */
+  double tail_wait_for_launch_ms; /* admitted -> launched                               */
+  double tail_launch_to_result_ms; /* launched -> result on the host                    */
+  double tail_mpix;           /*   size (megapixels)                                    */
+  double tail_batch;          /*   requests in their launch                             */
+} fbf_server_stats_t;
+
+/* fbf_server_create -- a server on CUDA device `device` filtering in precision form
+ * `precision` (FBF_FP32, FBF_FP16_TC, FBF_BF16_TC).  hbm_budget_bytes >= 1, max_batch >= 1
+ * (requests per launch; 1 = one request per launch), max_inflight >= 1.  The caller's
+ * current device is left unchanged.  Errors: FBF_EINVAL, FBF_ENOMEM, FBF_ECUDA. */
+int fbf_server_create(fbf_server_t* out, int device, int precision, uint64_t hbm_budget_bytes,
+                      int max_batch, int max_inflight);
+
+/* fbf_server_submit -- queue one request (any thread).  host_in / host_out: H x W float
+ * images, row-major, packed; page-locked host memory (for asynchronous copies), owned by
+ * the caller and untouched by it until the request's status is FBF_DONE or an error.
+ * theta, sigma, R, K, eps: as fbf_plan (plans are created once per distinct set and kept).
+ * *ticket (may be NULL) names the request for fbf_server_poll.  Errors: FBF_EINVAL (bad
+ * arguments, an image larger than the budget), FBF_EUNSUPPORTED (radius beyond the form's
+ * limit), fbf_plan's errors. */
+int fbf_server_submit(fbf_server_t s, const float* host_in, float* host_out, int H, int W, double theta,
+                      double sigma, int R, int K, double eps, fbf_ticket_t* ticket);
+
+/* fbf_server_replay -- submit n requests at arrival_s[i] seconds after the call (arrivals
+ * sorted), from the calling thread, sleeping until each arrival: an open-loop load
+ * generator for benchmarks.  Plans are created before the clock starts.  Array arguments
+ * as fbf_server_submit's, one entry per request; tickets may be NULL. */
+int fbf_server_replay(fbf_server_t s, int n, const double* arrival_s, const float* const* host_in,
+                      float* const* host_out, const int* H, const int* W, const double* theta,
+                      const double* sigma, const int* R, const int* K, const double* eps,
+                      fbf_ticket_t* tickets);
+
+/* fbf_server_poll -- non-blocking: *status = FBF_PENDING, FBF_DONE or the error code the
+ * request ended with.  FBF_EINVAL for an unknown ticket. */
+int fbf_server_poll(fbf_server_t s, fbf_ticket_t ticket, int* status);
+
+/* fbf_server_drain -- wait until every submitted request has finished, at most timeout_s
+ * seconds (FBF_ETIMEDOUT). */
+int fbf_server_drain(fbf_server_t s, double timeout_s);
+
+/* fbf_server_stats -- counters and latency statistics of the finished requests. */
+int fbf_server_stats(fbf_server_t s, fbf_server_stats_t* out);
+
+/* fbf_server_destroy -- finish the queued requests, stop the worker, release everything
+ * (NULL ok). */
+int fbf_server_destroy(fbf_server_t s);
+
 /* fbf_last_error -- message for the last failing call on this thread ("" if none). */
 /*
  * fbf_brute_filter -- eq. (1) evaluated directly with the Gaussian range kernel of eq. (2)

@@ -40,6 +40,18 @@ _lock = threading.Lock()
 _c_double_p = ctypes.POINTER(ctypes.c_double)
 _c_int_p = ctypes.POINTER(ctypes.c_int)
 _c_void_pp = ctypes.POINTER(ctypes.c_void_p)
+_c_u64_p = ctypes.POINTER(ctypes.c_uint64)
+
+
+class ServerStats(ctypes.Structure):
+    """Mirror of fbf_server_stats_t."""
+    _fields_ = [("requests", ctypes.c_uint64), ("pixels", ctypes.c_uint64), ("launches", ctypes.c_uint64),
+                ("failed", ctypes.c_uint64), ("hbm_high_water", ctypes.c_uint64),
+                ("waited_for_budget", ctypes.c_uint64), ("max_inflight_seen", ctypes.c_uint32),
+                ("wall_s", ctypes.c_double), ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+                ("tail_requests", ctypes.c_double), ("tail_queued_ms", ctypes.c_double),
+                ("tail_wait_for_launch_ms", ctypes.c_double), ("tail_launch_to_result_ms", ctypes.c_double),
+                ("tail_mpix", ctypes.c_double), ("tail_batch", ctypes.c_double)]
 
 # name -> (restype, argtypes); mirrors include/fbf.h
 SIGNATURES = {
@@ -78,6 +90,18 @@ SIGNATURES = {
     "fbf_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_double]),
     "fbf_batch_pending": (ctypes.c_int, [ctypes.c_void_p, _c_int_p]),
     "fbf_batch_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "fbf_server_create": (ctypes.c_int, [_c_void_pp, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.c_int,
+                                         ctypes.c_int]),
+    "fbf_server_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                         ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                         ctypes.c_int, ctypes.c_double, _c_u64_p]),
+    "fbf_server_replay": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _c_double_p, _c_void_pp, _c_void_pp,
+                                         _c_int_p, _c_int_p, _c_double_p, _c_double_p, _c_int_p, _c_int_p,
+                                         _c_double_p, _c_u64_p]),
+    "fbf_server_poll": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, _c_int_p]),
+    "fbf_server_drain": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
+    "fbf_server_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ServerStats)]),
+    "fbf_server_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "fbf_device_errors": (ctypes.c_int, [_c_int_p, ctypes.c_int]),
     "fbf_last_error": (ctypes.c_char_p, []),
     "fbf_version": (ctypes.c_char_p, []),
@@ -203,6 +227,54 @@ def fbf_batch_pending(batch: int) -> int:
 
 def fbf_batch_destroy(batch: int) -> None:
     _check(lib().fbf_batch_destroy(batch), "fbf_batch_destroy")
+
+
+def fbf_server_create(device: int, precision: int, hbm_budget_bytes: int, max_batch: int,
+                      max_inflight: int) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().fbf_server_create(ctypes.byref(h), device, precision, hbm_budget_bytes, max_batch,
+                                   max_inflight), "fbf_server_create")
+    return h.value
+
+
+def fbf_server_submit(server: int, host_in: int, host_out: int, H: int, W: int, theta: float, sigma: float,
+                      R: int, K: int, eps: float = 0.0) -> int:
+    t = ctypes.c_uint64()
+    _check(lib().fbf_server_submit(server, host_in, host_out, H, W, theta, sigma, R, K, eps, ctypes.byref(t)),
+           "fbf_server_submit")
+    return t.value
+
+
+def fbf_server_replay(server: int, arrival_s, host_in, host_out, H, W, theta, sigma, R, K, eps) -> list:
+    n = len(arrival_s)
+    arr = lambda ct, xs: (ct * n)(*xs)   # noqa: E731
+    tickets = (ctypes.c_uint64 * n)()
+    _check(lib().fbf_server_replay(server, n, arr(ctypes.c_double, arrival_s), arr(ctypes.c_void_p, host_in),
+                                   arr(ctypes.c_void_p, host_out), arr(ctypes.c_int, H), arr(ctypes.c_int, W),
+                                   arr(ctypes.c_double, theta), arr(ctypes.c_double, sigma),
+                                   arr(ctypes.c_int, R), arr(ctypes.c_int, K), arr(ctypes.c_double, eps),
+                                   tickets), "fbf_server_replay")
+    return list(tickets)
+
+
+def fbf_server_poll(server: int, ticket: int) -> int:
+    st = ctypes.c_int()
+    _check(lib().fbf_server_poll(server, ticket, ctypes.byref(st)), "fbf_server_poll")
+    return st.value
+
+
+def fbf_server_drain(server: int, timeout_s: float = 60.0) -> None:
+    _check(lib().fbf_server_drain(server, timeout_s), "fbf_server_drain")
+
+
+def fbf_server_stats(server: int) -> dict:
+    st = ServerStats()
+    _check(lib().fbf_server_stats(server, ctypes.byref(st)), "fbf_server_stats")
+    return {name: getattr(st, name) for name, _ in ServerStats._fields_}
+
+
+def fbf_server_destroy(server: int) -> None:
+    _check(lib().fbf_server_destroy(server), "fbf_server_destroy")
 
 
 def fbf_device_errors(clear: bool = False) -> int:
@@ -397,6 +469,59 @@ class Batch:
     def close(self):
         if getattr(self, "handle", None):
             fbf_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Owns an ``fbf_server_t`` (continuous batching under an HBM budget, served by a native
+    worker thread).  Host tensors passed to ``submit`` / ``replay`` must be pinned, float32,
+    contiguous, and stay alive until their request is done."""
+
+    def __init__(self, precision: int = FBF_FP32, hbm_budget_bytes: int = 40 << 30, max_batch: int = 64,
+                 max_inflight: int = 2, device: int = 0):
+        self.handle = fbf_server_create(device, precision, hbm_budget_bytes, max_batch, max_inflight)
+
+    @staticmethod
+    def _host(t):
+        if not (t.is_pinned() and t.is_contiguous() and t.dtype.itemsize == 4):
+            raise ValueError("host images must be pinned, contiguous float32 tensors")
+        return t.data_ptr()
+
+    def submit(self, host_in, host_out, theta: float, sigma: float, K: int = 0, eps: float = 0.0,
+               R: int = 255) -> int:
+        H, W = host_in.shape
+        if tuple(host_out.shape) != (H, W):
+            raise ValueError("host_out must have the shape of host_in")
+        return fbf_server_submit(self.handle, self._host(host_in), self._host(host_out), H, W, theta, sigma,
+                                 R, K, eps)
+
+    def replay(self, arrivals, host_in, host_out, theta, sigma, K, eps=None, R: int = 255) -> list:
+        """Submit request i at arrivals[i] seconds after the call (open-loop load)."""
+        n = len(arrivals)
+        eps = eps if eps is not None else [0.0] * n
+        return fbf_server_replay(self.handle, list(arrivals), [self._host(x) for x in host_in],
+                                 [self._host(y) for y in host_out], [x.shape[0] for x in host_in],
+                                 [x.shape[1] for x in host_in], list(theta), list(sigma), [R] * n, list(K),
+                                 list(eps))
+
+    def poll(self, ticket: int) -> int:
+        return fbf_server_poll(self.handle, ticket)
+
+    def drain(self, timeout_s: float = 600.0) -> None:
+        fbf_server_drain(self.handle, timeout_s)
+
+    def stats(self) -> dict:
+        return fbf_server_stats(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            fbf_server_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -210,3 +210,25 @@ def test_brute_filter_argument_errors():
     assert L.fbf_brute_filter(x, y, 4, 4, 4, 2.0, 30.0, 0, None) == B.FBF_EINVAL
     assert L.fbf_brute_filter(x, x, 4, 4, 4, 2.0, 30.0, 255, None) == B.FBF_EINVAL   # overlap
     assert L.fbf_brute_filter(x, y, 4, 4, 4, 17.0, 30.0, 255, None) == B.FBF_EUNSUPPORTED   # r = 51
+
+def test_server_argument_errors():
+    """fbf_server_create rejects bad arguments before touching a device; the other entry
+    points reject a NULL server."""
+    import ctypes
+    from paper_1811_02168_gb300 import binding as B
+    L = B.lib()
+    h = ctypes.c_void_p()
+    assert L.fbf_server_create(ctypes.byref(h), 0, 99, 1 << 20, 4, 2) == B.FBF_EINVAL      # form
+    assert L.fbf_server_create(ctypes.byref(h), 0, B.FBF_FP32, 0, 4, 2) == B.FBF_EINVAL    # budget
+    assert L.fbf_server_create(ctypes.byref(h), 0, B.FBF_FP32, 1 << 20, 0, 2) == B.FBF_EINVAL
+    assert L.fbf_server_create(ctypes.byref(h), 0, B.FBF_FP32, 1 << 20, 4, 0) == B.FBF_EINVAL
+    assert L.fbf_server_create(None, 0, B.FBF_FP32, 1 << 20, 4, 2) == B.FBF_EINVAL
+    t = ctypes.c_uint64()
+    st = ctypes.c_int()
+    assert L.fbf_server_submit(None, None, None, 8, 8, 2.0, 30.0, 255, 4, 0.0, ctypes.byref(t)) == B.FBF_EINVAL
+    assert L.fbf_server_poll(None, 1, ctypes.byref(st)) == B.FBF_EINVAL
+    assert L.fbf_server_drain(None, 1.0) == B.FBF_EINVAL
+    assert L.fbf_server_stats(None, None) == B.FBF_EINVAL
+    assert L.fbf_server_destroy(None) == B.FBF_OK
+    assert ctypes.sizeof(B.ServerStats) == 128
+

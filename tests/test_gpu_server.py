@@ -1,0 +1,110 @@
+"""The native serving loop (fbf_server_*) on the GPU: every served result equals the same
+request filtered alone by fbf_filter (within the FP32 tolerance; only the order of
+split-tile partial sums can differ between a batched and a lone launch), whatever else
+was in flight; admission respects the HBM budget; max_batch = 1 gives one launch per
+request.  FP32 and the compensated BF16 tensor-core form."""
+import numpy as np
+import pytest
+
+from paper_1811_02168_gb300.synth import voronoi_image
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+TOL = 5e-3
+
+
+@pytest.fixture(scope="module")
+def B():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1811_02168_gb300 import build
+    build.build()
+    from paper_1811_02168_gb300 import binding
+    binding.lib()
+    return binding
+
+
+def _requests(n, seed):
+    rng = np.random.default_rng(seed)
+    out = []
+    t = 0.0
+    for i in range(n):
+        t += rng.exponential(0.002)
+        H, W = (int(v) for v in rng.integers(40, 400, 2))
+        out.append(dict(t=t, H=H, W=W, theta=float(rng.choice([2.0, 5.0, 10.0])),
+                        sigma=float(rng.choice([10.0, 30.0, 80.0])), K=int(rng.choice([4, 8])),
+                        img=voronoi_image(H, W, 8, 30.0, 10.0, seed=1000 + i)))
+    return out
+
+
+def _alone(B, plans, r, precision):
+    key = (r["theta"], r["sigma"], r["K"])
+    if key not in plans:
+        plans[key] = B.Plan(r["sigma"], 255, r["theta"], K=r["K"], precision=precision)
+    x = torch.from_numpy(r["img"]).cuda()
+    y = torch.empty_like(x)
+    B.fbf_filter(plans[key].handle, x.data_ptr(), y.data_ptr(), r["H"], r["W"], r["W"],
+                 torch.cuda.current_stream().cuda_stream)
+    return y.cpu()
+
+
+def _close(got, ref):
+    # ill-conditioned plans can produce large outputs; compare relative to their magnitude
+    return float((got - ref).abs().max()) <= TOL * max(1.0, float(ref.abs().max()) / 255.0)
+
+
+@pytest.mark.parametrize("form", ["fp32", "bf16_tc"])
+def test_served_equals_alone(B, form):
+    prec = B.FBF_FP32 if form == "fp32" else B.FBF_BF16_TC
+    reqs = _requests(40, 3)
+    hin = [torch.from_numpy(r["img"]).pin_memory() for r in reqs]
+    hout = [torch.full((r["H"], r["W"]), -1.0).pin_memory() for r in reqs]
+    srv = B.Server(precision=prec, hbm_budget_bytes=1 << 30, max_batch=8, max_inflight=2)
+    tickets = srv.replay([r["t"] for r in reqs], hin, hout, [r["theta"] for r in reqs],
+                         [r["sigma"] for r in reqs], [r["K"] for r in reqs])
+    srv.drain(120.0)
+    st = srv.stats()
+    assert all(srv.poll(t) == B.FBF_DONE for t in tickets)
+    srv.close()
+    assert st["requests"] == len(reqs) and st["failed"] == 0
+    assert st["launches"] < len(reqs)                    # requests were batched
+    assert st["pixels"] == sum(r["H"] * r["W"] for r in reqs)
+    assert 0 < st["p50_ms"] <= st["p99_ms"]
+    plans = {}
+    for r, y in zip(reqs, hout):
+        assert _close(y, _alone(B, plans, r, prec)), (r["H"], r["W"], r["theta"], r["sigma"], r["K"])
+
+
+def test_budget_and_one_request_per_launch(B):
+    reqs = _requests(16, 4)
+    img = voronoi_image(768, 768, 30, 30.0, 10.0, seed=2000)
+    for r in reqs:                                       # equal sizes: the budget holds exactly two
+        r["H"], r["W"], r["img"] = 768, 768, img
+    budget = 2 * 8 * 768 * 768
+    hin = [torch.from_numpy(img).pin_memory()] * len(reqs)
+    hout = [torch.zeros((768, 768)).pin_memory() for _ in reqs]
+    srv = B.Server(precision=B.FBF_FP32, hbm_budget_bytes=budget, max_batch=1, max_inflight=2)
+    # every request arrives at once: the budget, not the arrival rate, must hold them back
+    srv.replay([0.0] * len(reqs), hin, hout, [r["theta"] for r in reqs], [r["sigma"] for r in reqs],
+               [r["K"] for r in reqs])
+    srv.drain(120.0)
+    st = srv.stats()
+    srv.close()
+    assert st["requests"] == len(reqs)
+    assert st["launches"] == len(reqs)                   # max_batch = 1
+    assert st["hbm_high_water"] <= budget
+    assert st["waited_for_budget"] > 0
+    plans = {}
+    for r, y in zip(reqs, hout):
+        assert _close(y, _alone(B, plans, r, B.FBF_FP32))
+
+
+def test_errors(B):
+    srv = B.Server(precision=B.FBF_FP32, hbm_budget_bytes=1 << 20, max_batch=4, max_inflight=1)
+    x = torch.zeros((512, 512)).pin_memory()             # 2 MiB of device buffers > 1 MiB budget
+    with pytest.raises(B.FbfError) as e:
+        srv.submit(x, x.clone().pin_memory(), 3.0, 30.0, K=4)
+    assert e.value.code == B.FBF_EINVAL
+    with pytest.raises(B.FbfError):
+        srv.poll(12345)
+    srv.close()
