@@ -44,7 +44,9 @@ def _args():
                     help="length of the Poisson request stream for --workload serve")
     ap.add_argument("--serve-rate", type=float, default=500.0)
     ap.add_argument("--serve-idle-sleep", type=float, default=5e-5,
-                    help="seconds the serving loop sleeps when it has nothing to do (0: poll)")
+                    help="python loop: seconds it sleeps when it has nothing to do (0: poll)")
+    ap.add_argument("--serve-loop", choices=["native", "python"], default="native",
+                    help="serving loop: the library's (fbf_server_*) or serve.py's")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-rows", type=int, default=96, help="oracle sample: rows per sigma")
     return ap.parse_args()
@@ -798,8 +800,8 @@ def run_serve(a):
     # batching, against the plain FP32 form one request per launch; and FP32 with batching
     modes = (("continuous_batching", B.FBF_BF16_TC, True), ("one_at_a_time_fp32", B.FBF_FP32, False),
              ("continuous_batching_fp32", B.FBF_FP32, True))
-    backends = {prec: TorchBackend(B, precision=prec) for _, prec, _ in modes}
-    # warm-up: every plan, kernel configuration and allocator size class once
+    backends = {prec: TorchBackend(B, precision=prec) for _, prec, _ in modes} if a.serve_loop == "python" else {}
+    # python loop warm-up: every plan, kernel configuration and allocator size class once
     for be in backends.values():
         warm = [Request(i, 0.0, 512 + 7 * i, 512, th, sg, K)
                 for i, (th, sg, K) in enumerate([(th, sg, K) for th in (2.0, 5.0, 10.0) for sg in (10.0, 30.0, 80.0)
@@ -808,15 +810,45 @@ def run_serve(a):
             r.host_in = pool[0][:r.H * r.W].view(r.H, r.W)
             r.host_out = ring[:r.H * r.W].view(r.H, r.W)
         Server(be, 40 << 30, max_batch=64).run(warm)
+    warm_params = [(th, sg, K) for th in (2.0, 5.0, 10.0) for sg in (10.0, 30.0, 80.0) for K in (4, 8, 16)]
+
+    def native(prec, batching, reqs):
+        """The library's serving loop: warm-up on the same server (plans, memory pool,
+        kernels), statistics cleared, then the stream replayed at its arrival times."""
+        srv = B.Server(precision=prec, hbm_budget_bytes=40 << 30, max_batch=256 if batching else 1,
+                       max_inflight=2)
+        for i, (th, sg, K) in enumerate(warm_params):
+            n = (512 + 7 * i) * 512
+            srv.submit(pool[0][:n].view(-1, 512), ring[:n].view(-1, 512), th, sg, K=K)
+        srv.drain(600.0)
+        srv.reset_stats()
+        srv.replay([r.arrival for r in reqs], [r.host_in for r in reqs], [r.host_out for r in reqs],
+                   [r.theta for r in reqs], [r.sigma for r in reqs], [r.K for r in reqs])
+        srv.drain(600.0)
+        st = srv.stats()
+        srv.close()
+        return {"requests": st["requests"], "pixels": st["pixels"], "wall_s": st["wall_s"],
+                "mpix_per_s": st["pixels"] / st["wall_s"] / 1e6 if st["wall_s"] > 0 else float("nan"),
+                "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "launches": st["launches"],
+                "max_inflight": st["max_inflight_seen"], "hbm_high_water_bytes": st["hbm_high_water"],
+                "waited_for_budget": st["waited_for_budget"], "failed": st["failed"],
+                "slowest_1pct": {"requests": st["tail_requests"], "queued_ms": st["tail_queued_ms"],
+                                 "wait_for_launch_ms": st["tail_wait_for_launch_ms"],
+                                 "launch_to_result_ms": st["tail_launch_to_result_ms"],
+                                 "mpix": st["tail_mpix"], "batch_requests": st["tail_batch"]}}
+
     results = {}
     clocks = ClockSampler(0)
     clocks.start()
     for mode, prec, batching in modes:
         reqs = make_requests()
         torch.cuda.synchronize(dev)
-        st = Server(backends[prec], 40 << 30, max_batch=256, max_inflight=2, batching=batching).run(
-            reqs, idle_sleep=a.serve_idle_sleep)
-        results[mode] = st.summary()
+        if a.serve_loop == "native":
+            results[mode] = native(prec, batching, reqs)
+        else:
+            st = Server(backends[prec], 40 << 30, max_batch=256, max_inflight=2, batching=batching).run(
+                reqs, idle_sleep=a.serve_idle_sleep)
+            results[mode] = st.summary()
     clk = clocks.stop()
     cb = results["continuous_batching"]
     line = {
@@ -829,6 +861,9 @@ def run_serve(a):
                    "seconds": a.serve_seconds, "sides": [512, 4096], "hbm_budget_gb": 40,
                    "form": "bf16_tc (compensated BF16 stack on the tensor cores; FP32 accumulation)",
                    "baseline_form": "fp32, one request per launch",
+                   "loop": ("the library's serving loop (fbf_server_*, native worker thread; requests "
+                            "replayed at their arrival times by fbf_server_replay)" if a.serve_loop == "native"
+                            else "serve.py's Python loop over the batch API"),
                    "served": results,
                    "note": "value = served throughput of the continuous-batching run; below capacity it equals the offered load"},
         "e2e": {"value": cb["mpix_per_s"], "unit": "Mpix/s",

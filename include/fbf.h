@@ -286,6 +286,10 @@ int fbf_server_drain(fbf_server_t s, double timeout_s);
 /* fbf_server_stats -- counters and latency statistics of the finished requests. */
 int fbf_server_stats(fbf_server_t s, fbf_server_stats_t* out);
 
+/* fbf_server_reset_stats -- clear the counters and latencies (after a warm-up); FBF_EBUSY
+ * while requests are pending. */
+int fbf_server_reset_stats(fbf_server_t s);
+
 /* fbf_server_destroy -- finish the queued requests, stop the worker, release everything
  * (NULL ok). */
 int fbf_server_destroy(fbf_server_t s);

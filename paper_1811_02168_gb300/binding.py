@@ -101,6 +101,7 @@ SIGNATURES = {
     "fbf_server_poll": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, _c_int_p]),
     "fbf_server_drain": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
     "fbf_server_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ServerStats)]),
+    "fbf_server_reset_stats": (ctypes.c_int, [ctypes.c_void_p]),
     "fbf_server_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "fbf_device_errors": (ctypes.c_int, [_c_int_p, ctypes.c_int]),
     "fbf_last_error": (ctypes.c_char_p, []),
@@ -271,6 +272,10 @@ def fbf_server_stats(server: int) -> dict:
     st = ServerStats()
     _check(lib().fbf_server_stats(server, ctypes.byref(st)), "fbf_server_stats")
     return {name: getattr(st, name) for name, _ in ServerStats._fields_}
+
+
+def fbf_server_reset_stats(server: int) -> None:
+    _check(lib().fbf_server_reset_stats(server), "fbf_server_reset_stats")
 
 
 def fbf_server_destroy(server: int) -> None:
@@ -518,6 +523,9 @@ class Server:
 
     def stats(self) -> dict:
         return fbf_server_stats(self.handle)
+
+    def reset_stats(self) -> None:
+        fbf_server_reset_stats(self.handle)
 
     def close(self):
         if getattr(self, "handle", None):

@@ -458,6 +458,18 @@ int fbf_server_stats(fbf_server_t s, fbf_server_stats_t* out) {
   return FBF_OK;
 }
 
+int fbf_server_reset_stats(fbf_server_t s) {
+  if (!s) return fbf::set_error(FBF_EINVAL, "fbf_server_reset_stats: NULL server");
+  std::lock_guard<std::mutex> g(s->mu);
+  if (s->pending != 0) return fbf::set_error(FBF_EBUSY, "fbf_server_reset_stats: requests pending");
+  s->requests = s->pixels = s->launches = s->failed = s->waited = 0;
+  s->high_water = s->used;
+  s->max_inflight_seen = 0;
+  s->t_first = s->t_last = -1;
+  s->trace.clear();
+  return FBF_OK;
+}
+
 int fbf_server_destroy(fbf_server_t s) {
   if (!s) return FBF_OK;
   {

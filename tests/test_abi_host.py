@@ -229,6 +229,7 @@ def test_server_argument_errors():
     assert L.fbf_server_poll(None, 1, ctypes.byref(st)) == B.FBF_EINVAL
     assert L.fbf_server_drain(None, 1.0) == B.FBF_EINVAL
     assert L.fbf_server_stats(None, None) == B.FBF_EINVAL
+    assert L.fbf_server_reset_stats(None) == B.FBF_EINVAL
     assert L.fbf_server_destroy(None) == B.FBF_OK
     assert ctypes.sizeof(B.ServerStats) == 128
 
