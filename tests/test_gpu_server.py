@@ -25,11 +25,12 @@ def B():
 
 
 def _requests(n, seed):
+    """Bursts of ten simultaneous arrivals, 5 ms apart: the worker admits a burst's requests
+    while it issues their uploads (tens of microseconds), so they share launches."""
     rng = np.random.default_rng(seed)
     out = []
-    t = 0.0
     for i in range(n):
-        t += rng.exponential(0.002)
+        t = 0.005 * (i // 10)
         H, W = (int(v) for v in rng.integers(40, 400, 2))
         out.append(dict(t=t, H=H, W=W, theta=float(rng.choice([2.0, 5.0, 10.0])),
                         sigma=float(rng.choice([10.0, 30.0, 80.0])), K=int(rng.choice([4, 8])),
