@@ -157,6 +157,23 @@ int fbf_filter(fbf_plan_t plan, const float* d_in, float* d_out, int H, int W,
 int fbf_filter_noalloc(fbf_plan_t plan, const float* d_in, float* d_out, int H, int W,
                        size_t pitch_elems, void* cuda_stream);
 
+/*
+ * fbf_filter_host -- f_BF of one image from host memory to host memory: the end-to-end
+ * call (eq. (1) with phi_hat, as fbf_filter).  host_in / host_out: H x W floats, row stride
+ * pitch_elems (>= W); page-locked memory gives asynchronous copies (pageable memory works,
+ * with copies staged by the driver); host_out may be host_in (in place), but not partly
+ * overlap it.  The image is cut into up to four bands of whole tile rows, each with at least
+ * two tiles per SM (smaller images are one band): band b's rows are
+ * uploaded, its filter runs as soon as its rows and the first r rows of band b + 1 are on
+ * the device (reading halo rows from the whole image), and its result is copied back while
+ * later bands compute.  Runs on `cuda_stream` (plus two internal copy streams per stream)
+ * and returns when the result is on the host.  Device images are kept per (device, stream)
+ * and grown as needed.  Errors: as fbf_filter, FBF_ENOMEM when the device images cannot
+ * be allocated.
+ */
+int fbf_filter_host(fbf_plan_t plan, const float* host_in, float* host_out, int H, int W,
+                    size_t pitch_elems, void* cuda_stream);
+
 /* ---- batched form (many images in one persistent launch) ------------------------- */
 typedef struct fbf_batch_s* fbf_batch_t;
 typedef uint64_t fbf_ticket_t;

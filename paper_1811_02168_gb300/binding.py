@@ -90,6 +90,8 @@ SIGNATURES = {
     "fbf_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_double]),
     "fbf_batch_pending": (ctypes.c_int, [ctypes.c_void_p, _c_int_p]),
     "fbf_batch_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "fbf_filter_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                       ctypes.c_int, ctypes.c_size_t, ctypes.c_void_p]),
     "fbf_server_create": (ctypes.c_int, [_c_void_pp, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.c_int,
                                          ctypes.c_int]),
     "fbf_server_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
@@ -228,6 +230,11 @@ def fbf_batch_pending(batch: int) -> int:
 
 def fbf_batch_destroy(batch: int) -> None:
     _check(lib().fbf_batch_destroy(batch), "fbf_batch_destroy")
+
+
+def fbf_filter_host(plan: int, host_in: int, host_out: int, H: int, W: int, pitch_elems: int,
+                    stream: int = 0) -> None:
+    _check(lib().fbf_filter_host(plan, host_in, host_out, H, W, pitch_elems, stream), "fbf_filter_host")
 
 
 def fbf_server_create(device: int, precision: int, hbm_budget_bytes: int, max_batch: int,
@@ -399,20 +406,25 @@ def bilateral_filter(plan: Plan, image, out=None, stream=None):
     """f_BF of one 2-D float32 image.
 
     ``image`` is a torch tensor.  On the GPU it is filtered in place of memory on the
-    current (or given) stream and a device tensor is returned.  On the host it is copied
-    to the device (pinned staging), filtered, and copied back: the end-to-end path.
+    current (or given) stream and a device tensor is returned.  On the host it goes through
+    ``fbf_filter_host`` (uploads, band-wise filter and downloads overlapped; returns when the
+    result is on the host): the end-to-end path.
     """
     import torch
     if image.dim() != 2 or image.dtype != torch.float32:
         raise ValueError("image must be a 2-D float32 tensor")
-    host = not image.is_cuda
-    if host:
+    if not image.is_cuda:
         src = image if image.is_pinned() else image.pin_memory()
-        dev_in = src.to("cuda", non_blocking=True)
-    else:
-        dev_in = image
-    if dev_in.stride(1) != 1:
-        dev_in = dev_in.contiguous()
+        if src.stride(1) != 1:
+            src = src.contiguous().pin_memory()
+        H, W = src.shape
+        res = out if out is not None else torch.empty((H, W), dtype=torch.float32, pin_memory=True)
+        if res.is_cuda or res.stride(1) != 1 or res.stride(0) != src.stride(0):
+            raise ValueError("out must be a host tensor with the input's row stride")
+        st = stream if stream is not None else torch.cuda.current_stream()
+        fbf_filter_host(plan.handle, src.data_ptr(), res.data_ptr(), H, W, src.stride(0), st.cuda_stream)
+        return res
+    dev_in = image if image.stride(1) == 1 else image.contiguous()
     H, W = dev_in.shape
     dev_out = out if (out is not None and out.is_cuda) else torch.empty((H, W), device=dev_in.device,
                                                                         dtype=torch.float32)
@@ -421,11 +433,6 @@ def bilateral_filter(plan: Plan, image, out=None, stream=None):
     st = stream if stream is not None else torch.cuda.current_stream(dev_in.device)
     fbf_filter(plan.handle, dev_in.data_ptr(), dev_out.data_ptr(), H, W, dev_in.stride(0),
                st.cuda_stream)
-    if host:
-        res = out if out is not None else torch.empty((H, W), dtype=torch.float32, pin_memory=True)
-        res.copy_(dev_out, non_blocking=True)
-        st.synchronize()
-        return res
     return dev_out
 
 

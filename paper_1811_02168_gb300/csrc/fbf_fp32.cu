@@ -187,15 +187,18 @@ int kernel_slots(KernelFn fn, int nt, size_t smem, int dev, int* sms_out, int* o
   return FBF_OK;
 }
 
-Work single_work(const float* in, float* out, int H, int W, size_t pitch, int K, int TY) {
+Work single_work(const float* in, float* out, int H, int W, size_t pitch, int K, int TY, int row0 = 0,
+                 int rows = 0) {
+  if (rows <= 0) rows = H - row0;
   Work w{};
+  w.row0 = row0;
   w.in = in;
   w.out = out;
   w.pitch = (long long)pitch;
   w.H = H;
   w.W = W;
   w.tiles_x = (W + TX - 1) / TX;
-  w.tiles_y = (H + TY - 1) / TY;
+  w.tiles_y = (rows + TY - 1) / TY;
   w.K = K;
   w.wtile = 2 * K - 1;
   w.tiles = (long long)w.tiles_x * w.tiles_y;
@@ -207,7 +210,7 @@ Work single_work(const float* in, float* out, int H, int W, size_t pitch, int K,
 
 template <int RAD, int TY, int NT, int NY>
 int launch_cfg(const DeviceParams& dp, const float* in, float* out, int H, int W, size_t pitch,
-               cudaStream_t st) {
+               cudaStream_t st, int row0, int rows) {
   using C = Cfg<RAD, TY, NT, NY>;
   static int occ[64] = {0};
   static int sms[64] = {0};
@@ -233,7 +236,7 @@ int launch_cfg(const DeviceParams& dp, const float* in, float* out, int H, int W
                       "fbf_filter");
   if (rc != FBF_OK) return rc;
   const DeviceParams p = pad_params<RAD>(dp);
-  const Work w = single_work(in, out, H, W, pitch, dp.K, TY);
+  const Work w = single_work(in, out, H, W, pitch, dp.K, TY, row0, rows);
   if (w.tiles > (1LL << 30)) return set_error(FBF_EUNSUPPORTED, "fbf_filter: image too large");
   Scratch sc{};
   sc.wtot = w.tiles * w.wtile;
@@ -257,19 +260,26 @@ int launch_cfg(const DeviceParams& dp, const float* in, float* out, int H, int W
 
 }  // namespace
 
+int fp32_tile_rows(int r) {
+  if (r <= 6) return 112;
+  if (r <= 15) return 96;
+  if (r <= 30) return 128;
+  return 64;
+}
+
 int launch_fp32(const DeviceParams& dp, const float* in, float* out, int H, int W, size_t pitch,
-                void* stream) {
+                void* stream, int row0, int rows) {
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const int r = dp.r;
   // Tile heights keep TY + 2r just under a whole number of x-pass rounds (4 rows per
   // warp); radii above 15 need more registers for their taps and use 256 threads.
-  if (r <= 3) return launch_cfg<3, 112, 512, 7>(dp, in, out, H, W, pitch, st);
-  if (r <= 6) return launch_cfg<6, 112, 512, 7>(dp, in, out, H, W, pitch, st);
-  if (r <= 9) return launch_cfg<9, 96, 512, 6>(dp, in, out, H, W, pitch, st);
-  if (r <= 15) return launch_cfg<15, 96, 512, 6>(dp, in, out, H, W, pitch, st);
-  if (r <= 24) return launch_cfg<24, 128, 256, 16>(dp, in, out, H, W, pitch, st);
-  if (r <= 30) return launch_cfg<30, 128, 256, 16>(dp, in, out, H, W, pitch, st);
-  if (r <= 48) return launch_cfg<48, 64, 128, 16>(dp, in, out, H, W, pitch, st);
+  if (r <= 3) return launch_cfg<3, 112, 512, 7>(dp, in, out, H, W, pitch, st, row0, rows);
+  if (r <= 6) return launch_cfg<6, 112, 512, 7>(dp, in, out, H, W, pitch, st, row0, rows);
+  if (r <= 9) return launch_cfg<9, 96, 512, 6>(dp, in, out, H, W, pitch, st, row0, rows);
+  if (r <= 15) return launch_cfg<15, 96, 512, 6>(dp, in, out, H, W, pitch, st, row0, rows);
+  if (r <= 24) return launch_cfg<24, 128, 256, 16>(dp, in, out, H, W, pitch, st, row0, rows);
+  if (r <= 30) return launch_cfg<30, 128, 256, 16>(dp, in, out, H, W, pitch, st, row0, rows);
+  if (r <= 48) return launch_cfg<48, 64, 128, 16>(dp, in, out, H, W, pitch, st, row0, rows);
   return set_error(FBF_EUNSUPPORTED, "fbf_filter: radius too large");
 }
 

@@ -128,6 +128,7 @@ struct Work {
   long long wstart;                   // weighted offset of the image's first unit
   int counter_base;                   // index of the image's first tile counter
   int param_idx;                      // index of the image's DeviceParams (work-lists)
+  int row0;                           // image row of the first tile row (a band of rows)
 };
 
 struct Scratch {
@@ -340,7 +341,7 @@ __device__ __forceinline__ void fbf_body(const Src& src, const Scratch& sc) {
     if (tid == 0 && (img < img_end || (img == img_end && u < u_end))) {
       const Work w0 = src.work(img);
       const long long t0 = u / w0.K;
-      tma_load_box(fhb, src.map, (int)(t0 % w0.tiles_x) * TX - C::TMA_RX, (int)(t0 / w0.tiles_x) * TY - RAD,
+      tma_load_box(fhb, src.map, (int)(t0 % w0.tiles_x) * TX - C::TMA_RX, w0.row0 + (int)(t0 / w0.tiles_x) * TY - RAD,
                    fbar, C::TMA_FH * 4);
     }
   }
@@ -368,7 +369,7 @@ __device__ __forceinline__ void fbf_body(const Src& src, const Scratch& sc) {
     const int kb = (int)(u - t * K);
     const int ke = (img == img_end && t == u_end / K) ? (int)(u_end - t * K) : K;
     const int tx0 = (int)(t % wk.tiles_x) * TX;
-    const int ty0 = (int)(t / wk.tiles_x) * TY;
+    const int ty0 = wk.row0 + (int)(t / wk.tiles_x) * TY;
 
     // f of the tile plus halo (rows padded to whole x-pass rounds); kOutside marks
     // pixels outside the image.  The tile uses the term tables when all its values are
@@ -442,7 +443,7 @@ __device__ __forceinline__ void fbf_body(const Src& src, const Scratch& sc) {
         const long long tn = un / K;
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         tma_load_box(fhb + (fb ^ 1) * C::TMA_FH, src.map, (int)(tn % wk.tiles_x) * TX - C::TMA_RX,
-                     (int)(tn / wk.tiles_x) * TY - RAD, fbar + (fb ^ 1), C::TMA_FH * 4);
+                     wk.row0 + (int)(tn / wk.tiles_x) * TY - RAD, fbar + (fb ^ 1), C::TMA_FH * 4);
       }
       fb ^= 1;
     }

@@ -74,15 +74,19 @@ void clear_error();
 
 // ---- kernels --------------------------------------------------------------------------
 // FP32 fused kernel launcher (fbf_fp32.cu).
+// row0 / rows (rows = 0: all): filter only output rows [row0, row0 + rows) of the H x W
+// image (a band; row0 a multiple of the configuration's tile height), reading halo rows
+// from the whole image.
 int launch_fp32(const DeviceParams& dp, const float* in, float* out, int H, int W,
-                size_t pitch, void* stream);
+                size_t pitch, void* stream, int row0 = 0, int rows = 0);
+int fp32_tile_rows(int r);                  // tile height of the FP32 configuration serving r
 // Per-(device, stream) scratch: `counters` zeroed ints (left at zero by every launch) and
 // `partial_bytes` of partial sums; grown with cudaMalloc when too small.
 int get_workspace(int dev, cudaStream_t_ st, size_t partial_bytes, size_t counters,
                   float** partial, int** counter);
 // Tensor-core forms (fbf_tc.cu): precision FBF_FP16_TC or FBF_BF16_TC.
 int launch_tc(const DeviceParams& dp, const float* in, float* out, int H, int W, size_t pitch,
-              void* stream, int precision);
+              void* stream, int precision, int row0 = 0, int rows = 0);
 // Device error word of the tensor-core kernels (bit 0: a bounded wait gave up).
 int device_errors(int* flags, int clear);
 // FP32 single-image kernels' error word (bit 1: a TMA wait gave up), and the reset of the

@@ -797,7 +797,7 @@ __device__ __forceinline__ void tc_body(const Src& src, const Scratch& sc) {
       const int ke = (img == img_end && t == u_end / K) ? (int)(u_end - t * K) : K;
       const int np = frag_pairs(kb, ke);
       const int tx0 = (int)(t % cw.tiles_x) * TILE_X;
-      const int ty0 = (int)(t / cw.tiles_x) * C::TY;
+      const int ty0 = cw.row0 + (int)(t / cw.tiles_x) * C::TY;
 
       // f of the tile + halo as bytes (zero outside the image and in the padding); the tile
       // takes the table path when every pixel is an integer in [0, min(R, 255)]
@@ -944,8 +944,9 @@ fbf_tc_batch_kernel(const DeviceParams* __restrict__ prm, const Work* __restrict
 
 template <int RAD, typename T>
 int launch_rad(const DeviceParams& dp, const float* in, float* out, int H, int W, size_t pitch,
-               cudaStream_t st) {
+               cudaStream_t st, int row0, int rows) {
   using C = TcCfg<RAD, Parts<T>::value>;
+  if (rows <= 0) rows = H - row0;
   static int occ[64] = {0};
   static int sms[64] = {0};
   int dev = 0;
@@ -979,7 +980,8 @@ int launch_rad(const DeviceParams& dp, const float* in, float* out, int H, int W
   w.H = H;
   w.W = W;
   w.tiles_x = (W + TILE_X - 1) / TILE_X;
-  w.tiles_y = (H + C::TY - 1) / C::TY;
+  w.tiles_y = (rows + C::TY - 1) / C::TY;
+  w.row0 = row0;
   w.K = dp.K;
   w.wtile = 2 * dp.K - 1;
   w.tiles = (long long)w.tiles_x * w.tiles_y;
@@ -1028,21 +1030,21 @@ int launch_batch_rad(const DeviceParams* dparams, const Work* dwork, int n, long
 
 template <typename T>
 int launch_type(const DeviceParams& dp, const float* in, float* out, int H, int W, size_t pitch,
-                cudaStream_t st) {
+                cudaStream_t st, int row0, int rows) {
   const int r = dp.r;
-  if (r <= 6) return launch_rad<6, T>(dp, in, out, H, W, pitch, st);
-  if (r <= 15) return launch_rad<15, T>(dp, in, out, H, W, pitch, st);
-  if (r <= 30) return launch_rad<30, T>(dp, in, out, H, W, pitch, st);
+  if (r <= 6) return launch_rad<6, T>(dp, in, out, H, W, pitch, st, row0, rows);
+  if (r <= 15) return launch_rad<15, T>(dp, in, out, H, W, pitch, st, row0, rows);
+  if (r <= 30) return launch_rad<30, T>(dp, in, out, H, W, pitch, st, row0, rows);
   return set_error(FBF_EUNSUPPORTED, "fbf_filter: the tensor-core forms support r = ceil(3 theta) <= 30");
 }
 
 }  // namespace tc
 
 int launch_tc(const DeviceParams& dp, const float* in, float* out, int H, int W, size_t pitch,
-              void* stream, int precision) {
+              void* stream, int precision, int row0, int rows) {
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  if (precision == FBF_BF16_TC) return tc::launch_type<__nv_bfloat16>(dp, in, out, H, W, pitch, st);
-  return tc::launch_type<__half>(dp, in, out, H, W, pitch, st);
+  if (precision == FBF_BF16_TC) return tc::launch_type<__nv_bfloat16>(dp, in, out, H, W, pitch, st, row0, rows);
+  return tc::launch_type<__half>(dp, in, out, H, W, pitch, st, row0, rows);
 }
 
 int launch_tc_batch(int rad, int precision, const DeviceParams* dparams, const fp32::Work* dwork, int n, long long wtot,

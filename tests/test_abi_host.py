@@ -233,3 +233,17 @@ def test_server_argument_errors():
     assert L.fbf_server_destroy(None) == B.FBF_OK
     assert ctypes.sizeof(B.ServerStats) == 128
 
+def test_filter_host_argument_errors():
+    """fbf_filter_host rejects bad arguments before any device work."""
+    import ctypes
+    from paper_1811_02168_gb300 import binding as B
+    L = B.lib()
+    p = B.Plan(30.0, 255, 2.0, K=4)
+    buf = (ctypes.c_float * 64)()
+    a = ctypes.addressof(buf)
+    assert L.fbf_filter_host(None, a, a, 8, 8, 8, None) == B.FBF_EINVAL
+    assert L.fbf_filter_host(p.handle, None, a, 8, 8, 8, None) == B.FBF_EINVAL
+    assert L.fbf_filter_host(p.handle, a, a, 0, 8, 8, None) == B.FBF_EINVAL
+    assert L.fbf_filter_host(p.handle, a, a, 8, 8, 7, None) == B.FBF_EINVAL       # pitch < W
+    assert L.fbf_filter_host(p.handle, a, a + 4, 8, 8, 8, None) == B.FBF_EINVAL   # partial overlap
+
