@@ -160,10 +160,13 @@ int fbf_filter_noalloc(fbf_plan_t plan, const float* d_in, float* d_out, int H, 
 /*
  * fbf_filter_host -- f_BF of one image from host memory to host memory: the end-to-end
  * call (eq. (1) with phi_hat, as fbf_filter).  host_in / host_out: H x W floats, row stride
- * pitch_elems (>= W); page-locked memory gives asynchronous copies (pageable memory works,
- * with copies staged by the driver); host_out may be host_in (in place), but not partly
- * overlap it.  The image is cut into up to four bands of whole tile rows, each with at least
- * two tiles per SM (smaller images are one band): band b's rows are
+ * pitch_elems (>= W); host_out may be host_in (in place), but not partly overlap it.  When
+ * both are distinct page-locked buffers mapped into the device's address space (e.g. from
+ * cudaHostAlloc under unified addressing), the kernel reads the image and writes the result
+ * through the host link directly, with no staging copies.  Otherwise the image is staged
+ * through device memory (pageable memory works, with copies staged by the driver) in up to
+ * four bands of whole tile rows, each with at least two tiles per SM (smaller images are one
+ * band): band b's rows are
  * uploaded, its filter runs as soon as its rows and the first r rows of band b + 1 are on
  * the device (reading halo rows from the whole image), and its result is copied back while
  * later bands compute.  Runs on `cuda_stream` (plus two internal copy streams per stream)

@@ -152,10 +152,18 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 
 // Tensor map of the image for the TMA staging of the f halo: FP32, dims {W, H}, row stride
 // pitch, box {box_w, box_h}, NaN for elements outside the image.  False when the image does
-// not allow one (base not 16-byte aligned, row stride not a multiple of 16 bytes) or the
-// driver has no encoder; the caller then stages with plain loads.
+// not allow one (base not 16-byte aligned, row stride not a multiple of 16 bytes, not in
+// device memory) or the driver has no encoder; the caller then stages with plain loads.
 bool encode_f_map(CUtensorMap* map, const float* in, int H, int W, size_t pitch, int box_w, int box_h) {
   if ((reinterpret_cast<uintptr_t>(in) & 15) != 0 || (pitch * sizeof(float)) % 16 != 0) return false;
+  // device memory only: images the kernel reads from host memory (mapped, page-locked) take
+  // the plain loads
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, in) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) return false;
   const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!enc) return false;
   const cuuint64_t dims[2] = {(cuuint64_t)W, (cuuint64_t)H};

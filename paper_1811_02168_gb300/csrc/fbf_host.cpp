@@ -1,5 +1,10 @@
-// fbf_filter_host: one image from host memory to host memory, copies overlapped with the
-// filter.
+// fbf_filter_host: one image from host memory to host memory.
+//
+// Page-locked buffers (mapped into the device's address space, distinct): the kernel reads
+// the image and writes the result through the host link directly, with no staging copies;
+// the transfers spread over the launch instead of preceding and following it.  Otherwise
+// (pageable memory, or in place) the image is staged through device memory, with the
+// copies overlapped with the filter as follows.
 //
 // The image is cut into B bands of whole tile rows (1 to 4 bands, each with at least two tiles
 // per SM; small images are one band).  On an upload stream each
@@ -134,6 +139,25 @@ extern "C" int fbf_filter_host(fbf_plan_t plan, const float* host_in, float* hos
   int nbands = 0;
   for (int t = 0; t < tile_rows && nbands < kMaxBands; t += per) b0[nbands++] = t * ty;
   b0[nbands] = H;
+
+  // page-locked, mapped and distinct buffers: the kernel works on host memory directly
+  if (host_in != host_out) {
+    cudaPointerAttributes ai, ao;
+    const bool known = cudaPointerGetAttributes(&ai, host_in) == cudaSuccess &&
+                       cudaPointerGetAttributes(&ao, host_out) == cudaSuccess;
+    if (!known) cudaGetLastError();
+    if (known && ai.type == cudaMemoryTypeHost && ao.type == cudaMemoryTypeHost && ai.devicePointer &&
+        ao.devicePointer) {
+      const float* din = static_cast<const float*>(ai.devicePointer);
+      float* dout = static_cast<float*>(ao.devicePointer);
+      int rc0 = (prec == FBF_FP32) ? fbf::launch_fp32(p->dp, din, dout, H, W, pitch_elems, st)
+                                   : fbf::launch_tc(p->dp, din, dout, H, W, pitch_elems, st, prec);
+      if (rc0 != FBF_OK) return rc0;
+      e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) return fail("synchronise", e);
+      return FBF_OK;
+    }
+  }
 
   const size_t dp = ((size_t)W + 3) / 4 * 4;        // device row stride: 16-byte rows
   HostCtx* c = context_of(dev, st);

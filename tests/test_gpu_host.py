@@ -1,5 +1,6 @@
-"""fbf_filter_host (host memory in, host memory out, band-wise overlap of copies and filter)
-gives fbf_filter's result.  Bands are whole tile rows and each band's launch reads its halo
+"""fbf_filter_host (host memory in, host memory out: read and written by the kernel directly
+for distinct page-locked buffers, else staged in bands with the copies overlapped) gives
+fbf_filter's result.  Bands are whole tile rows and each band's launch reads its halo
 rows from the whole image, so the only difference from one launch over the whole image is
 the order of split-tile partial sums (stream-K splits fall elsewhere).  Each result is
 within its own rounding error of the exact one, which small bilateral denominators amplify
@@ -7,9 +8,9 @@ within its own rounding error of the exact one, which small bilateral denominato
 much: the bound is 1e-3 gray levels for FP32, a fifth of its tolerance (observed: 2e-4),
 and 1e-2 for the tensor-core forms, whose errors against the oracle are larger (up to 4.2
 for FP16_TC at r = 30; observed difference 1.2e-3).
-Cases: one band and several, a ragged last band, widths that are not a multiple of 4 (the
-device rows are padded), a host pitch above the width, in place, FP32 and the tensor-core
-forms; one case also against the FP64 oracle."""
+Cases: page-locked (direct), in place and pageable (staged: one band and several, a ragged
+last band, widths that are not a multiple of 4 so the device rows are padded), a host pitch
+above the width, FP32 and the tensor-core forms; one case also against the FP64 oracle."""
 import numpy as np
 import pytest
 
@@ -42,12 +43,16 @@ def _device(B, plan, img):
     return y.cpu().numpy()
 
 
-def _host(B, plan, img, pitch=None, inplace=False):
+def _host(B, plan, img, pitch=None, inplace=False, pinned=True):
+    """pinned: the kernel reads and writes the host buffers directly; pageable (or in place):
+    the image is staged through device memory in bands."""
     H, W = img.shape
     pitch = pitch or W
-    src = torch.full((H, pitch), -3.0).pin_memory()
+    src = torch.full((H, pitch), -3.0)
+    src = src.pin_memory() if pinned else src
     src[:, :W] = torch.from_numpy(img)
-    dst = src if inplace else torch.full((H, pitch), -9.0).pin_memory()
+    dst = src if inplace else torch.full((H, pitch), -9.0)
+    dst = dst.pin_memory() if (pinned and not inplace) else dst
     B.fbf_filter_host(plan.handle, src.data_ptr(), dst.data_ptr(), H, W, pitch,
                       torch.cuda.current_stream().cuda_stream)
     out = dst.numpy()
@@ -73,6 +78,8 @@ def test_host_call_equals_device_call(B, prec, theta, sigma, K, H, W):
     got = _host(B, plan, img, pitch=W + 13)
     assert float(np.abs(got - ref).max()) <= tol
     got = _host(B, plan, img, inplace=True)
+    assert float(np.abs(got - ref).max()) <= tol
+    got = _host(B, plan, img, pitch=W + 3, pinned=False)
     assert float(np.abs(got - ref).max()) <= tol
     assert B.fbf_device_errors(True) == 0
 
