@@ -87,3 +87,19 @@ def test_tma_non_integer_image(B):
     ref99 = ofl.fourier_bf(img[:, :99].astype(np.float64), 4.0, op.c, op.T)
     assert float(np.abs(pitched - ref).max()) <= TOL
     assert float(np.abs(packed - ref99).max()) <= TOL
+
+
+@pytest.mark.parametrize("H,W,theta", [(1, 4, 2.0), (2, 8, 3.0), (61, 4, 3.0), (5, 8, 5.0),
+                                       (3, 200, 5.0), (33, 32, 5.0), (130, 96, 1.5)])
+def test_tma_edge_shapes(B, H, W, theta):
+    """Degenerate shapes on the TMA path (aligned rows, r <= 15): a single row, images
+    smaller than the window and than one box, so that most of each box is outside the image
+    (NaN-filled); bit-identical to the plain staging and within the tolerance of the oracle."""
+    img = voronoi_image(H, W, 5, 30.0, 10.0, seed=H * 1000 + W + 7)
+    plan = B.Plan(30.0, 255, theta, K=5)
+    tma = _run(B, plan, img, W, 0)          # aligned: TMA
+    plain = _run(B, plan, img, W, 1)        # base one float past alignment: plain
+    assert np.array_equal(tma, plain)
+    op = ofit.make_plan(30.0, 255, K=5)
+    ref = ofl.fourier_bf(img.astype(np.float64), theta, op.c, op.T)
+    assert float(np.abs(tma - ref).max()) <= TOL
