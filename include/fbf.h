@@ -52,13 +52,15 @@ extern "C" {
    the channel stack and its taps as 16-bit operands; its result is rounded to nearest
    TF32 and contracted with TF32 taps in the y pass.  Recombination and divide are FP32.
    Errors against the FP64 oracle grow where the bilateral denominator is small (a pixel
-   unlike its whole window): see the precision section of the design notes.            */
-#define FBF_FP16_TC    1   /* FP16 stack and taps (fastest; ~0.13 max error on typical
-                              8-bit images, up to ~1.8 at small denominators)          */
+   unlike its whole window, so that the denominator is little more than the centre tap):
+   absolute errors of numerator and denominator are divided by it.                       */
+#define FBF_FP16_TC    1   /* FP16 stack and taps (fastest; 0.03-0.28 max error on typical
+                              8-bit images, up to ~4 at small denominators)            */
 #define FBF_BF16_TC    2   /* compensated BF16 stack: every operand value and x-pass tap
                               is a hi + lo BF16 pair (three x-pass products) and the
-                              x-pass result is TF32 hi + FP16 lo; FP32-class accuracy
-                              (~0.002 on 8-bit images, 0.05 at small denominators)      */
+                              x-pass result is TF32 hi + FP16 lo (max error ~0.004 on
+                              8-bit images, 0.08 at small denominators, against 0.003
+                              for FBF_FP32)                                             */
 
 /* ---- flags (fbf_plan's `flags`) ----------------------------------------------- */
 #define FBF_FLAG_FIXED_PERIOD 1  /* T = R (fixed period, the FBF model the paper
