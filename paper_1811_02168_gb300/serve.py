@@ -1,15 +1,19 @@
-"""Continuous-batching server for bilateral-filtering requests.
+"""Continuous-batching server for bilateral-filtering requests: the Python model of the
+library's native serving loop (``fbf_server_*``, a worker thread in the library, which the
+benchmark uses).  This one keeps the same policy with a pluggable device backend, so the
+admission, budget and batching logic can be tested on the CPU (``FakeBackend``), and runs
+on the GPU through ``TorchBackend``.
 
 Requests (an image plus theta, sigma and K) arrive over time.  The loop:
 
   * admits waiting requests in arrival order while their device buffers (input + output,
     8 bytes per pixel) fit the HBM budget and the next launch has room;
-  * starts the device copy of each admitted image at once (copy stream);
+  * starts the device copy of each admitted image at once (upload stream);
   * launches everything admitted so far as ONE batched launch (compute stream, one
     persistent kernel per radius class) whenever fewer than ``max_inflight`` launches are
     on the GPU -- requests that arrive while others run join the next launch instead of
     waiting for a fixed batch to fill (continuous batching);
-  * copies results back (copy stream, after the launch) and, when a launch's results are on
+  * copies results back (download stream, after the launch) and, when a launch's results are on
     the host, records each request's latency (completion - arrival) and frees its budget.
 
 Plans (the fitted K, T, c per (theta, sigma, K)) are cached, so the FP64 fit runs once per
