@@ -6,10 +6,13 @@ Default workload (the sigma sweep): one 1024 x 1024 synthetic 8-bit image (Voron
 200 cells, ramp 40, noise 10, seed 1000), theta = 5 (31 x 31 window), sigma in
 {10, 30, 80}, K chosen by Algorithm 1 at eps = 0.01, FP32 form.  One step filters the
 image once per sigma (3 launches, 3.15 Mpix).  Inputs are resident in HBM; L2 is flushed
-(256 MiB write) before every timed step, outside the timed region.
+(256 MiB write) before every timed step, outside the timed region.  The end-to-end figure
+(`e2e`) runs the same steps from pinned host tensors through the C ABI's host-buffer call,
+wall clock.  The CPU baseline is the FP64 oracle as it stands, in row bands on every host
+core.
 
 Output: one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle instead
-(bounded sample per step) with the same metric and config.
+(the same sharding, a bounded sample per step) with the same metric and config.
 """
 from __future__ import annotations
 
