@@ -2,7 +2,7 @@
 request filtered alone by fbf_filter (within the FP32 tolerance; only the order of
 split-tile partial sums can differ between a batched and a lone launch), whatever else
 was in flight; admission respects the HBM budget; max_batch = 1 gives one launch per
-request.  FP32 and the compensated BF16 tensor-core form."""
+request.  FP32 and both tensor-core forms."""
 import numpy as np
 import pytest
 
@@ -54,9 +54,9 @@ def _close(got, ref):
     return float((got - ref).abs().max()) <= TOL * max(1.0, float(ref.abs().max()) / 255.0)
 
 
-@pytest.mark.parametrize("form", ["fp32", "bf16_tc"])
+@pytest.mark.parametrize("form", ["fp32", "bf16_tc", "fp16_tc"])
 def test_served_equals_alone(B, form):
-    prec = B.FBF_FP32 if form == "fp32" else B.FBF_BF16_TC
+    prec = {"fp32": B.FBF_FP32, "bf16_tc": B.FBF_BF16_TC, "fp16_tc": B.FBF_FP16_TC}[form]
     reqs = _requests(40, 3)
     hin = [torch.from_numpy(r["img"]).pin_memory() for r in reqs]
     hout = [torch.full((r["H"], r["W"]), -1.0).pin_memory() for r in reqs]

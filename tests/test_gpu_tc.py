@@ -104,3 +104,19 @@ def test_bf16_non_integer_input(B):
     ref = ofl.fourier_bf(img.astype(np.float64), 5.0, op.c, op.T)
     assert float(np.abs(_run(B, plan, img) - ref).max()) <= TOL["bf16"]
     assert B.fbf_device_errors() == 0
+
+
+@pytest.mark.parametrize("form", ["fp16", "bf16"])
+def test_tc_non_gaussian_range_kernel(B, form):
+    """The tensor-core forms take any fitted range kernel (the fitter's samples, Section II's
+    closing remark on other kernels): an exponential kernel against the oracle's filter with
+    the same fit."""
+    R, s = 255, 25.0
+    kern = lambda t: np.exp(-np.abs(t) / s)  # noqa: E731
+    img = voronoi_image(130, 150, 9, 30.0, 10.0, seed=17)
+    prec = B.FBF_FP16_TC if form == "fp16" else B.FBF_BF16_TC
+    plan = B.Plan(None, R, 3.0, K=10, samples=kern(np.arange(-R, R + 1)), precision=prec)
+    op = ofit.make_plan(None, R, K=10, kernel=kern)
+    ref = ofl.fourier_bf(img.astype(np.float64), 3.0, op.c, op.T)
+    assert float(np.abs(_run(B, plan, img) - ref).max()) <= TOL[form]
+    assert B.fbf_device_errors() == 0
