@@ -172,9 +172,11 @@ int fbf_filter_noalloc(fbf_plan_t plan, const float* d_in, float* d_out, int H, 
  * uploaded, its filter runs as soon as its rows and the first r rows of band b + 1 are on
  * the device (reading halo rows from the whole image), and its result is copied back while
  * later bands compute.  Runs on `cuda_stream` (plus two internal copy streams per stream)
- * and returns when the result is on the host.  Device images are kept per (device, stream)
- * and grown as needed.  Errors: as fbf_filter, FBF_ENOMEM when the device images cannot
- * be allocated.
+ * and returns when the result is on the host.  Device images, copy streams and events are
+ * kept per (device, stream), grown as needed and held until the process exits (a caller
+ * that cycles through many streams holds one set per stream).  Errors: as fbf_filter,
+ * FBF_ENOMEM when the device images cannot be allocated; on an error the call returns only
+ * after the copies it queued have finished.
  */
 int fbf_filter_host(fbf_plan_t plan, const float* host_in, float* host_out, int H, int W,
                     size_t pitch_elems, void* cuda_stream);
@@ -213,12 +215,13 @@ int fbf_submit(fbf_batch_t batch, fbf_plan_t plan, const float* d_in, float* d_o
                size_t pitch_elems, fbf_ticket_t* ticket);
 
 /* fbf_launch -- upload the work-list of the queued images and launch them on `cuda_stream`
- * (asynchronous); the queue is emptied.  A no-op when nothing is queued. */
+ * (asynchronous); the queue is emptied, also when the call fails (the queued images'
+ * outputs are then undefined; submit them again).  A no-op when nothing is queued. */
 int fbf_launch(fbf_batch_t batch, void* cuda_stream);
 
 /* fbf_batch_capture -- instead of launching, record the queued images' launch (work-list
  * copy + kernels) as a CUDA graph owned by the batch, replacing any earlier one; the queue
- * is emptied.  Tuning and allocation happen before the capture. */
+ * is emptied, also when the call fails.  Tuning and allocation happen before the capture. */
 int fbf_batch_capture(fbf_batch_t batch, void* cuda_stream);
 
 /* fbf_batch_replay -- launch the captured graph on `cuda_stream` (same pointers and sizes,

@@ -55,11 +55,11 @@ struct BatchCfg {
     if (!occ[dev]) {
       cudaError_t e = cudaFuncSetAttribute(fbf_fp32_batch_kernel<RAD, TY, NT, NY>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM_BYTES);
-      if (e != cudaSuccess) return set_error(FBF_ECUDA, std::string("fbf_launch: ") + cudaGetErrorString(e));
+      if (e != cudaSuccess) return set_error(FBF_ECUDA, std::string("fbf_batch: ") + cudaGetErrorString(e));
       int n = 0;
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fbf_fp32_batch_kernel<RAD, TY, NT, NY>, NT,
                                                         C::SMEM_BYTES);
-      if (e != cudaSuccess || n < 1) return set_error(FBF_ECUDA, "fbf_launch: kernel does not fit on an SM");
+      if (e != cudaSuccess || n < 1) return set_error(FBF_ECUDA, "fbf_batch: kernel does not fit on an SM");
       int s = 0;
       cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev);
       sms[dev] = s;
@@ -88,7 +88,7 @@ struct BatchCfg {
     sc.counter = counter;
     fbf_fp32_batch_kernel<RAD, TY, NT, NY><<<(unsigned)g, NT, C::SMEM_BYTES, st>>>(dparams, dwork, n, sc);
     cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return set_error(FBF_ECUDA, std::string("fbf_launch: ") + cudaGetErrorString(e));
+    if (e != cudaSuccess) return set_error(FBF_ECUDA, std::string("fbf_batch: ") + cudaGetErrorString(e));
     return FBF_OK;
   }
 };
@@ -253,9 +253,9 @@ namespace {
 int ensure_device(Batch* b) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return set_error(FBF_ECUDA, std::string("fbf_launch: ") + cudaGetErrorString(e));
-  if (dev < 0 || dev >= 64) return set_error(FBF_EUNSUPPORTED, "fbf_launch: device index >= 64");
-  if (b->dev >= 0 && b->dev != dev) return set_error(FBF_EINVAL, "fbf_launch: batch used on another device");
+  if (e != cudaSuccess) return set_error(FBF_ECUDA, std::string("fbf_batch: ") + cudaGetErrorString(e));
+  if (dev < 0 || dev >= 64) return set_error(FBF_EUNSUPPORTED, "fbf_batch: device index >= 64");
+  if (b->dev >= 0 && b->dev != dev) return set_error(FBF_EINVAL, "fbf_batch: batch used on another device");
   b->dev = dev;
   return FBF_OK;
 }
@@ -275,7 +275,7 @@ int build_lists(Batch* b, std::vector<ClassPlan>* out, size_t* bytes) {
   std::map<int, ClassPlan> by;
   for (const Pending& pd : b->pending) {
     const int cls = class_of(pd.plan->r, pd.plan->precision);
-    if (cls < 0) return set_error(FBF_EUNSUPPORTED, "fbf_launch: radius too large");
+    if (cls < 0) return set_error(FBF_EUNSUPPORTED, "fbf_batch: radius too large");
     ClassPlan& cp = by[cls];
     cp.cls = cls;
     // one DeviceParams per distinct plan in the class
@@ -337,12 +337,12 @@ int ensure_buffers(Batch* b, size_t list_bytes, size_t counters, size_t partial)
   Batch::ListBuf& lb = b->ring[b->slot];
   if (lb.pending) {   // the copy that last read this slot must have run
     e = cudaEventSynchronize(lb.copied);
-    if (e != cudaSuccess) return set_error(FBF_ECUDA, std::string("fbf_launch: ") + cudaGetErrorString(e));
+    if (e != cudaSuccess) return set_error(FBF_ECUDA, std::string("fbf_batch: ") + cudaGetErrorString(e));
     lb.pending = false;
   }
   if (!lb.copied) {
     e = cudaEventCreateWithFlags(&lb.copied, cudaEventDisableTiming);
-    if (e != cudaSuccess) return set_error(FBF_ECUDA, std::string("fbf_launch: ") + cudaGetErrorString(e));
+    if (e != cudaSuccess) return set_error(FBF_ECUDA, std::string("fbf_batch: ") + cudaGetErrorString(e));
   }
   if (lb.cap < list_bytes) {
     if (lb.h) cudaFreeHost(lb.h);
@@ -350,9 +350,9 @@ int ensure_buffers(Batch* b, size_t list_bytes, size_t counters, size_t partial)
     lb.h = lb.d = nullptr;
     lb.cap = 0;
     e = cudaMallocHost(&lb.h, list_bytes);
-    if (e != cudaSuccess) return set_error(FBF_ENOMEM, std::string("fbf_launch: ") + cudaGetErrorString(e));
+    if (e != cudaSuccess) return set_error(FBF_ENOMEM, std::string("fbf_batch: ") + cudaGetErrorString(e));
     e = cudaMalloc(&lb.d, list_bytes);
-    if (e != cudaSuccess) return set_error(FBF_ENOMEM, std::string("fbf_launch: ") + cudaGetErrorString(e));
+    if (e != cudaSuccess) return set_error(FBF_ENOMEM, std::string("fbf_batch: ") + cudaGetErrorString(e));
     lb.cap = list_bytes;
   }
   if (b->counter_cap < counters || b->partial_cap < partial) {
@@ -362,9 +362,9 @@ int ensure_buffers(Batch* b, size_t list_bytes, size_t counters, size_t partial)
     const size_t pc = partial + partial / 2;
     const size_t cbytes = ((cc * sizeof(int) + 255) / 256) * 256;
     e = cudaMalloc(&b->d_scratch, cbytes + pc);
-    if (e != cudaSuccess) return set_error(FBF_ENOMEM, std::string("fbf_launch: ") + cudaGetErrorString(e));
+    if (e != cudaSuccess) return set_error(FBF_ENOMEM, std::string("fbf_batch: ") + cudaGetErrorString(e));
     e = cudaMemset(b->d_scratch, 0, cbytes);   // counters start at zero; launches leave them at zero
-    if (e != cudaSuccess) return set_error(FBF_ECUDA, std::string("fbf_launch: ") + cudaGetErrorString(e));
+    if (e != cudaSuccess) return set_error(FBF_ECUDA, std::string("fbf_batch: ") + cudaGetErrorString(e));
     b->counter_cap = cc;
     b->partial_cap = pc;
   }
@@ -389,10 +389,10 @@ int launch_classes(Batch* b, const std::vector<ClassPlan>& cps, size_t list_byte
                    bool capturing) {
   Batch::ListBuf& lb = b->ring[b->slot];
   cudaError_t e = cudaMemcpyAsync(lb.d, lb.h, list_bytes, cudaMemcpyHostToDevice, st);
-  if (e != cudaSuccess) return set_error(FBF_ECUDA, std::string("fbf_launch: ") + cudaGetErrorString(e));
+  if (e != cudaSuccess) return set_error(FBF_ECUDA, std::string("fbf_batch: ") + cudaGetErrorString(e));
   if (!capturing) {
     e = cudaEventRecord(lb.copied, st);
-    if (e != cudaSuccess) return set_error(FBF_ECUDA, std::string("fbf_launch: ") + cudaGetErrorString(e));
+    if (e != cudaSuccess) return set_error(FBF_ECUDA, std::string("fbf_batch: ") + cudaGetErrorString(e));
     lb.pending = true;
   }
   char* d = static_cast<char*>(lb.d);
@@ -482,10 +482,10 @@ int record_generation(Batch* b, cudaStream_t st, unsigned long long* gen_out) {
     b->free_events.pop_back();
   } else {
     cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
-    if (e != cudaSuccess) return set_error(FBF_ECUDA, std::string("fbf_launch: ") + cudaGetErrorString(e));
+    if (e != cudaSuccess) return set_error(FBF_ECUDA, std::string("fbf_batch: ") + cudaGetErrorString(e));
   }
   cudaError_t e = cudaEventRecord(ev, st);
-  if (e != cudaSuccess) return set_error(FBF_ECUDA, std::string("fbf_launch: ") + cudaGetErrorString(e));
+  if (e != cudaSuccess) return set_error(FBF_ECUDA, std::string("fbf_batch: ") + cudaGetErrorString(e));
   const unsigned long long g = b->next_gen++;
   b->gens.push_back({g, ev});
   *gen_out = g;
@@ -566,11 +566,20 @@ int fbf_submit(fbf_batch_t batch, fbf_plan_t plan, const float* d_in, float* d_o
   return FBF_OK;
 }
 
+// Empties a batch's queue when the call that took its images returns, whether or not the
+// launch or capture succeeded: after an error the caller may free the images' buffers, so
+// they must not stay queued for the next launch.
+struct EmptyQueueOnExit {
+  fbf::Batch& b;
+  ~EmptyQueueOnExit() { b.pending.clear(); }
+};
+
 int fbf_launch(fbf_batch_t batch, void* cuda_stream) {
   if (!batch) return fbf::set_error(FBF_EINVAL, "fbf_launch: batch is NULL");
   fbf::Batch& b = batch->b;
   std::lock_guard<std::mutex> lk(b.mu);
   if (b.pending.empty()) return FBF_OK;
+  EmptyQueueOnExit empty_on_exit{b};
   int rc = fbf::ensure_device(&b);
   if (rc != FBF_OK) return rc;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
@@ -585,7 +594,6 @@ int fbf_launch(fbf_batch_t batch, void* cuda_stream) {
   rc = fbf::record_generation(&b, st, &g);
   if (rc != FBF_OK) return rc;
   ++b.launches;
-  b.pending.clear();
   return FBF_OK;
 }
 
@@ -594,6 +602,7 @@ int fbf_batch_capture(fbf_batch_t batch, void* cuda_stream) {
   fbf::Batch& b = batch->b;
   std::lock_guard<std::mutex> lk(b.mu);
   if (b.pending.empty()) return fbf::set_error(FBF_EINVAL, "fbf_batch_capture: no submitted images");
+  EmptyQueueOnExit empty_on_exit{b};
   int rc = fbf::ensure_device(&b);
   if (rc != FBF_OK) return rc;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
@@ -625,7 +634,6 @@ int fbf_batch_capture(fbf_batch_t batch, void* cuda_stream) {
   e = cudaGraphInstantiate(&b.graph, graph, 0);
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) return fbf::set_error(FBF_ECUDA, std::string("fbf_batch_capture: ") + cudaGetErrorString(e));
-  b.pending.clear();
   return FBF_OK;
 }
 

@@ -173,16 +173,24 @@ extern "C" int fbf_filter_host(fbf_plan_t plan, const float* host_in, float* hos
       return cudaMemcpyAsync(dst, src, wb * (size_t)n, kind, s);
     return cudaMemcpy2DAsync(dst, dst_pitch, src, src_pitch, wb, n, kind, s);
   };
+  // on an error after copies were queued, wait for them (best effort) before returning, so
+  // that no copy still reads or writes the caller's buffers once the call has returned
+  auto drain = [&](int code) {
+    cudaStreamSynchronize(st);
+    cudaStreamSynchronize(c->up);
+    cudaStreamSynchronize(c->down);
+    return code;
+  };
   if (nbands == 1) {
     // one band: nothing to overlap, so everything stays on the caller's stream
     e = copy_rows(c->d_in, dpb, host_in, hp, H, cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return fail("upload", e);
+    if (e != cudaSuccess) return drain(fail("upload", e));
     rc = (prec == FBF_FP32) ? fbf::launch_fp32(p->dp, c->d_in, c->d_out, H, W, dp, st)
                             : fbf::launch_tc(p->dp, c->d_in, c->d_out, H, W, dp, st, prec);
-    if (rc != FBF_OK) return rc;
+    if (rc != FBF_OK) return drain(rc);
     e = copy_rows(host_out, hp, c->d_out, dpb, H, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return fail("download", e);
+    if (e != cudaSuccess) return drain(fail("download", e));
     return FBF_OK;
   }
   // uploads start once the caller's stream has reached this call
@@ -198,25 +206,25 @@ extern "C" int fbf_filter_host(fbf_plan_t plan, const float* host_in, float* hos
                     hp, b0[b + 1] - b0[b] - head, cudaMemcpyHostToDevice, c->up);
     if (e == cudaSuccess) e = cudaEventRecord(c->ev_in[b], c->up);
   }
-  if (e != cudaSuccess) return fail("upload", e);
+  if (e != cudaSuccess) return drain(fail("upload", e));
   for (int b = 0; b < nbands; ++b) {
     // rows [b0 - r, b1 + r) must be on the device: band b and the head of band b + 1 (the
     // upload stream is in order, so band b's event also covers the bands above it)
     e = cudaStreamWaitEvent(st, c->ev_in[b], 0);
     if (e == cudaSuccess && b + 1 < nbands) e = cudaStreamWaitEvent(st, c->ev_head[b + 1], 0);
-    if (e != cudaSuccess) return fail("order", e);
+    if (e != cudaSuccess) return drain(fail("order", e));
     rc = (prec == FBF_FP32)
              ? fbf::launch_fp32(p->dp, c->d_in, c->d_out, H, W, dp, st, b0[b], b0[b + 1] - b0[b])
              : fbf::launch_tc(p->dp, c->d_in, c->d_out, H, W, dp, st, prec, b0[b], b0[b + 1] - b0[b]);
-    if (rc != FBF_OK) return rc;
+    if (rc != FBF_OK) return drain(rc);
     e = cudaEventRecord(c->ev_k[b], st);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(c->down, c->ev_k[b], 0);
     if (e == cudaSuccess)
       e = copy_rows(host_out + (size_t)b0[b] * pitch_elems, hp, c->d_out + (size_t)b0[b] * dp, dpb,
                     b0[b + 1] - b0[b], cudaMemcpyDeviceToHost, c->down);
-    if (e != cudaSuccess) return fail("download", e);
+    if (e != cudaSuccess) return drain(fail("download", e));
   }
   e = cudaStreamSynchronize(c->down);
-  if (e != cudaSuccess) return fail("synchronise", e);
+  if (e != cudaSuccess) return drain(fail("synchronise", e));
   return FBF_OK;
 }

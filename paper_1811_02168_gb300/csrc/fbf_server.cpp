@@ -57,6 +57,7 @@ struct Req {
   cudaEvent_t up = nullptr;       // upload complete
   int batch = 0;                  // requests in its launch
   bool deferred = false;          // counted once in waited_for_budget
+  bool released = false;          // its device buffers' frees are enqueued
 };
 
 struct Launch {
@@ -103,15 +104,40 @@ struct fbf_server_s {
 
 namespace {
 
+// After a failed upload or launch: wait (best effort) for the copies and kernels that may
+// still use a request's buffers, then give the buffers back to the pool (called without
+// the lock).
+void release_after_error(fbf_server_s* s, const std::vector<Req*>& reqs) {
+  cudaStreamSynchronize(s->up);
+  cudaStreamSynchronize(s->comp);
+  cudaStreamSynchronize(s->down);
+  for (Req* r : reqs) {
+    if (r->released) continue;
+    if (r->d_in) cudaFreeAsync(r->d_in, s->down);
+    if (r->d_out) cudaFreeAsync(r->d_out, s->down);
+    r->d_in = r->d_out = nullptr;
+    r->released = true;
+  }
+  cudaStreamSynchronize(s->down);
+}
+
 // Device buffers and the upload of one admitted request (called without the lock).
 int upload(fbf_server_s* s, Req* r) {
   const size_t n = (size_t)r->H * r->W * sizeof(float);
-  cudaError_t e = cudaMallocFromPoolAsync(reinterpret_cast<void**>(&r->d_in), n, s->pool, s->up);
-  if (e == cudaSuccess) e = cudaMallocFromPoolAsync(reinterpret_cast<void**>(&r->d_out), n, s->pool, s->up);
+  void* a = nullptr;
+  void* b = nullptr;
+  cudaError_t e = cudaMallocFromPoolAsync(&a, n, s->pool, s->up);
+  if (e == cudaSuccess) r->d_in = static_cast<float*>(a);
+  if (e == cudaSuccess) e = cudaMallocFromPoolAsync(&b, n, s->pool, s->up);
+  if (e == cudaSuccess) r->d_out = static_cast<float*>(b);
   if (e == cudaSuccess) e = cudaMemcpyAsync(r->d_in, r->host_in, n, cudaMemcpyHostToDevice, s->up);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r->up, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventRecord(r->up, s->up);
-  if (e != cudaSuccess) return fbf::set_error(FBF_ECUDA, std::string("fbf_server: upload: ") + cudaGetErrorString(e));
+  if (e != cudaSuccess) {
+    const int rc = fbf::set_error(FBF_ECUDA, std::string("fbf_server: upload: ") + cudaGetErrorString(e));
+    release_after_error(s, {r});
+    return rc;
+  }
   return FBF_OK;
 }
 
@@ -137,7 +163,12 @@ int launch(fbf_server_s* s, Launch& L) {
     const size_t n = (size_t)r->H * r->W * sizeof(float);
     e = cudaMemcpyAsync(r->host_out, r->d_out, n, cudaMemcpyDeviceToHost, s->down);
     if (e == cudaSuccess) e = cudaFreeAsync(r->d_in, s->down);
+    if (e == cudaSuccess) r->d_in = nullptr;
     if (e == cudaSuccess) e = cudaFreeAsync(r->d_out, s->down);
+    if (e == cudaSuccess) {
+      r->d_out = nullptr;
+      r->released = true;
+    }
   }
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventRecord(L.done, s->down);
@@ -199,10 +230,17 @@ void worker_main(fbf_server_s* s) {
       const int rc = launch(s, L);
       lk.lock();
       if (rc != FBF_OK) {
-        // the stream state is unknown: wait for what was enqueued before giving the buffers up
+        // the stream state is unknown: wait for what was enqueued, free what was not freed.
+        // fbf_launch empties the batch's queue on failure too; if an fbf_submit failed
+        // before it, images stay queued, and the batch (idle now) is made anew
         lk.unlock();
-        cudaStreamSynchronize(s->comp);
-        cudaStreamSynchronize(s->down);
+        release_after_error(s, L.reqs);
+        int queued = 0;
+        if (!s->batch || fbf_batch_pending(s->batch, &queued) != FBF_OK || queued > 0) {
+          if (s->batch) fbf_batch_destroy(s->batch);
+          s->batch = nullptr;
+          fbf_batch_create(&s->batch, s->max_batch, 0);   // if this fails, launches fail
+        }
         lk.lock();
         if (L.done) cudaEventDestroy(L.done);
         for (Req* r : L.reqs) retire(s, r, rc, now_s());

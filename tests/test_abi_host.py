@@ -197,6 +197,26 @@ def test_batch_host_side_queue_and_bounded_wait():
         B.fbf_batch_create(0, 0)
 
 
+def test_failed_launch_empties_the_queue():
+    """A launch or capture that fails (here: no CUDA device) still empties the queue, so
+    images whose buffers the caller frees after the error are never launched later.  The
+    pointers are fake, so this runs only where no GPU is visible."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("fake device pointers: only without a GPU")
+    p = B.Plan(30.0, 255, 3.0, K=4)
+    b = B.fbf_batch_create(2, 0)
+    try:
+        for call in (lambda: B.fbf_launch(b, 0), lambda: B.fbf_batch_capture(b, 0)):
+            B.fbf_submit(b, p.handle, 1 << 20, 1 << 30, 16, 16, 16)
+            assert B.fbf_batch_pending(b) == 1
+            with pytest.raises(B.FbfError):
+                call()
+            assert B.fbf_batch_pending(b) == 0
+    finally:
+        B.fbf_batch_destroy(b)
+
+
 def test_brute_filter_argument_errors():
     from paper_1811_02168_gb300 import binding as B
     L = B.lib()
