@@ -533,7 +533,7 @@ struct fbf_batch_s {
 
 extern "C" {
 
-int fbf_batch_create(fbf_batch_t* out, int max_images, int flags) {
+int fbf_batch_create(fbf_batch_t* out, int max_images, int flags) try {
   if (!out) return fbf::set_error(FBF_EINVAL, "fbf_batch_create: out is NULL");
   *out = nullptr;
   if (max_images < 1) return fbf::set_error(FBF_EINVAL, "fbf_batch_create: max_images must be >= 1");
@@ -544,10 +544,10 @@ int fbf_batch_create(fbf_batch_t* out, int max_images, int flags) {
   h->b.flags = flags;
   *out = h;
   return FBF_OK;
-}
+} FBF_ABI_CATCH("fbf_batch_create")
 
 int fbf_submit(fbf_batch_t batch, fbf_plan_t plan, const float* d_in, float* d_out, int H, int W,
-               size_t pitch_elems, fbf_ticket_t* ticket) {
+               size_t pitch_elems, fbf_ticket_t* ticket) try {
   if (!batch || !plan) return fbf::set_error(FBF_EINVAL, "fbf_submit: NULL batch or plan");
   if (!d_in || !d_out) return fbf::set_error(FBF_EINVAL, "fbf_submit: NULL image pointer");
   if (H < 1 || W < 1) return fbf::set_error(FBF_EINVAL, "fbf_submit: H and W must be >= 1");
@@ -564,7 +564,7 @@ int fbf_submit(fbf_batch_t batch, fbf_plan_t plan, const float* d_in, float* d_o
   b.pending.push_back({p, d_in, d_out, H, W, pitch_elems});
   if (ticket) *ticket = (fbf_ticket_t)b.next_gen;
   return FBF_OK;
-}
+} FBF_ABI_CATCH("fbf_submit")
 
 // Empties a batch's queue when the call that took its images returns, whether or not the
 // launch or capture succeeded: after an error the caller may free the images' buffers, so
@@ -574,7 +574,7 @@ struct EmptyQueueOnExit {
   ~EmptyQueueOnExit() { b.pending.clear(); }
 };
 
-int fbf_launch(fbf_batch_t batch, void* cuda_stream) {
+int fbf_launch(fbf_batch_t batch, void* cuda_stream) try {
   if (!batch) return fbf::set_error(FBF_EINVAL, "fbf_launch: batch is NULL");
   fbf::Batch& b = batch->b;
   std::lock_guard<std::mutex> lk(b.mu);
@@ -595,9 +595,9 @@ int fbf_launch(fbf_batch_t batch, void* cuda_stream) {
   if (rc != FBF_OK) return rc;
   ++b.launches;
   return FBF_OK;
-}
+} FBF_ABI_CATCH("fbf_launch")
 
-int fbf_batch_capture(fbf_batch_t batch, void* cuda_stream) {
+int fbf_batch_capture(fbf_batch_t batch, void* cuda_stream) try {
   if (!batch) return fbf::set_error(FBF_EINVAL, "fbf_batch_capture: batch is NULL");
   fbf::Batch& b = batch->b;
   std::lock_guard<std::mutex> lk(b.mu);
@@ -635,9 +635,9 @@ int fbf_batch_capture(fbf_batch_t batch, void* cuda_stream) {
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) return fbf::set_error(FBF_ECUDA, std::string("fbf_batch_capture: ") + cudaGetErrorString(e));
   return FBF_OK;
-}
+} FBF_ABI_CATCH("fbf_batch_capture")
 
-int fbf_batch_replay(fbf_batch_t batch, void* cuda_stream, fbf_ticket_t* ticket) {
+int fbf_batch_replay(fbf_batch_t batch, void* cuda_stream, fbf_ticket_t* ticket) try {
   if (!batch) return fbf::set_error(FBF_EINVAL, "fbf_batch_replay: batch is NULL");
   fbf::Batch& b = batch->b;
   std::lock_guard<std::mutex> lk(b.mu);
@@ -650,9 +650,9 @@ int fbf_batch_replay(fbf_batch_t batch, void* cuda_stream, fbf_ticket_t* ticket)
   if (rc != FBF_OK) return rc;
   if (ticket) *ticket = (fbf_ticket_t)g;
   return FBF_OK;
-}
+} FBF_ABI_CATCH("fbf_batch_replay")
 
-int fbf_poll(fbf_batch_t batch, fbf_ticket_t ticket, int* status) {
+int fbf_poll(fbf_batch_t batch, fbf_ticket_t ticket, int* status) try {
   if (!batch || !status) return fbf::set_error(FBF_EINVAL, "fbf_poll: NULL argument");
   fbf::Batch& b = batch->b;
   std::lock_guard<std::mutex> lk(b.mu);
@@ -660,9 +660,9 @@ int fbf_poll(fbf_batch_t batch, fbf_ticket_t ticket, int* status) {
   if (s != FBF_DONE && s != FBF_PENDING) return s;
   *status = s;
   return FBF_OK;
-}
+} FBF_ABI_CATCH("fbf_poll")
 
-int fbf_wait(fbf_batch_t batch, fbf_ticket_t ticket, double timeout_s) {
+int fbf_wait(fbf_batch_t batch, fbf_ticket_t ticket, double timeout_s) try {
   if (!batch) return fbf::set_error(FBF_EINVAL, "fbf_wait: batch is NULL");
   if (!(timeout_s >= 0)) return fbf::set_error(FBF_EINVAL, "fbf_wait: timeout must be >= 0");
   const auto t0 = std::chrono::steady_clock::now();
@@ -678,16 +678,16 @@ int fbf_wait(fbf_batch_t batch, fbf_ticket_t ticket, double timeout_s) {
     if (el >= timeout_s) return fbf::set_error(FBF_ETIMEDOUT, "fbf_wait: timed out");
     std::this_thread::sleep_for(std::chrono::microseconds(50));
   }
-}
+} FBF_ABI_CATCH("fbf_wait")
 
-int fbf_batch_pending(fbf_batch_t batch, int* n) {
+int fbf_batch_pending(fbf_batch_t batch, int* n) try {
   if (!batch || !n) return fbf::set_error(FBF_EINVAL, "fbf_batch_pending: NULL argument");
   std::lock_guard<std::mutex> lk(batch->b.mu);
   *n = (int)batch->b.pending.size();
   return FBF_OK;
-}
+} FBF_ABI_CATCH("fbf_batch_pending")
 
-int fbf_batch_destroy(fbf_batch_t batch) {
+int fbf_batch_destroy(fbf_batch_t batch) try {
   if (!batch) return FBF_OK;
   fbf::Batch& b = batch->b;
   for (auto& g : b.gens) {
@@ -705,6 +705,6 @@ int fbf_batch_destroy(fbf_batch_t batch) {
   if (b.d_scratch) cudaFree(b.d_scratch);
   delete batch;
   return FBF_OK;
-}
+} FBF_ABI_CATCH("fbf_batch_destroy")
 
 }  // extern "C"

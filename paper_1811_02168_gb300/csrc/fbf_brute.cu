@@ -145,7 +145,7 @@ int launch(const Params& p, cudaStream_t st) {
 }  // namespace fbf
 
 extern "C" int fbf_brute_filter(const float* d_in, float* d_out, int H, int W, size_t pitch_elems,
-                                double theta, double sigma, int R, void* cuda_stream) {
+                                double theta, double sigma, int R, void* cuda_stream) try {
   using namespace fbf;
   if (!d_in || !d_out) return set_error(FBF_EINVAL, "fbf_brute_filter: NULL image pointer");
   if (H < 1 || W < 1) return set_error(FBF_EINVAL, "fbf_brute_filter: H and W must be >= 1");
@@ -179,4 +179,4 @@ extern "C" int fbf_brute_filter(const float* d_in, float* d_out, int H, int W, s
     case 30: return brute::launch<30>(p, st);
     default: return brute::launch<48>(p, st);
   }
-}
+} FBF_ABI_CATCH("fbf_brute_filter")

@@ -1,8 +1,10 @@
 // C ABI: plans, parameter read-back, errors (host only; the launches live in the .cu files).
 #include <cmath>
 #include <cstring>
+#include <memory>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "fbf_internal.h"
 
@@ -61,7 +63,7 @@ int build_plan(fbf_plan_t* out, const double* b, int R, double theta, int K, dou
     return fbf::set_error(FBF_EUNSUPPORTED, "fbf_plan: the tensor-core forms support r <= FBF_MAX_RADIUS_TC");
   if (K > FBF_MAX_K) return fbf::set_error(FBF_EUNSUPPORTED, "fbf_plan: K exceeds FBF_MAX_K");
 
-  fbf_plan_s* h = new (std::nothrow) fbf_plan_s();
+  std::unique_ptr<fbf_plan_s> h(new (std::nothrow) fbf_plan_s());
   if (!h) return fbf::set_error(FBF_ENOMEM, "fbf_plan: out of host memory");
   Plan& p = h->p;
   p.sigma = sigma;
@@ -73,9 +75,9 @@ int build_plan(fbf_plan_t* out, const double* b, int R, double theta, int K, dou
   std::string msg;
   int T_fixed = (flags & FBF_FLAG_FIXED_PERIOD) ? R : (T_given > 0 ? T_given : 0);
   int rc = fbf::fit_range_kernel(b, R, K, eps, T_fixed, &p.fit, &msg);
-  if (rc != FBF_OK) { delete h; return fbf::set_error(rc, "fbf_plan: " + msg); }
-  if (p.fit.K > FBF_MAX_K) { delete h; return fbf::set_error(FBF_EUNSUPPORTED, "fbf_plan: fitted K exceeds FBF_MAX_K"); }
-  if (2L * p.fit.T + 1 > FBF_MAX_PERIOD) { delete h; return fbf::set_error(FBF_EUNSUPPORTED, "fbf_plan: period exceeds FBF_MAX_PERIOD"); }
+  if (rc != FBF_OK) return fbf::set_error(rc, "fbf_plan: " + msg);
+  if (p.fit.K > FBF_MAX_K) return fbf::set_error(FBF_EUNSUPPORTED, "fbf_plan: fitted K exceeds FBF_MAX_K");
+  if (2L * p.fit.T + 1 > FBF_MAX_PERIOD) return fbf::set_error(FBF_EUNSUPPORTED, "fbf_plan: period exceeds FBF_MAX_PERIOD");
 
   // device constants
   fbf::DeviceParams& d = p.dp;
@@ -101,7 +103,7 @@ int build_plan(fbf_plan_t* out, const double* b, int R, double theta, int K, dou
   double gs = 0;
   for (int i = -r; i <= r; ++i) gs += std::exp(-(double)i * i / (2.0 * theta * theta));
   for (int i = -r; i <= r; ++i) d.g[i + r] = (float)(std::exp(-(double)i * i / (2.0 * theta * theta)) / gs);
-  *out = h;
+  *out = h.release();
   fbf::clear_error();
   return FBF_OK;
 }
@@ -113,7 +115,7 @@ using fbf::build_plan;
 extern "C" {
 
 int fbf_plan(fbf_plan_t* out, double sigma, int R, double theta, int K, double eps,
-             int precision, int flags) {
+             int precision, int flags) try {
   if (!(sigma > 0) || !std::isfinite(sigma)) {
     if (out) *out = nullptr;
     return fbf::set_error(FBF_EINVAL, "fbf_plan: sigma must be > 0");
@@ -122,17 +124,13 @@ int fbf_plan(fbf_plan_t* out, double sigma, int R, double theta, int K, double e
     if (out) *out = nullptr;
     return fbf::set_error(FBF_EINVAL, "fbf_plan: R out of range");
   }
-  std::string b_err;
-  double* b = new (std::nothrow) double[2 * R + 1];
-  if (!b) return fbf::set_error(FBF_ENOMEM, "fbf_plan: out of host memory");
+  std::vector<double> b(2 * (size_t)R + 1);
   for (int t = -R; t <= R; ++t) b[t + R] = std::exp(-(double)t * t / (2.0 * sigma * sigma));
-  int rc = build_plan(out, b, R, theta, K, eps, precision, flags, sigma, 0);
-  delete[] b;
-  return rc;
-}
+  return build_plan(out, b.data(), R, theta, K, eps, precision, flags, sigma, 0);
+} FBF_ABI_CATCH("fbf_plan")
 
 int fbf_plan_from_samples(fbf_plan_t* out, const double* b, int R, double theta, int K,
-                          double eps, int precision, int flags) {
+                          double eps, int precision, int flags) try {
   if (!b) {
     if (out) *out = nullptr;
     return fbf::set_error(FBF_EINVAL, "fbf_plan_from_samples: b is NULL");
@@ -142,9 +140,9 @@ int fbf_plan_from_samples(fbf_plan_t* out, const double* b, int R, double theta,
     return fbf::set_error(FBF_EINVAL, "fbf_plan_from_samples: R out of range");
   }
   return build_plan(out, b, R, theta, K, eps, precision, flags, NAN, 0);
-}
+} FBF_ABI_CATCH("fbf_plan_from_samples")
 
-int fbf_plan_info(fbf_plan_t plan, int* K, int* T, double* c, double* E, double* delta_max) {
+int fbf_plan_info(fbf_plan_t plan, int* K, int* T, double* c, double* E, double* delta_max) try {
   if (!plan) return fbf::set_error(FBF_EINVAL, "fbf_plan_info: plan is NULL");
   const fbf::FitResult& f = plan->p.fit;
   if (K) *K = f.K;
@@ -153,21 +151,21 @@ int fbf_plan_info(fbf_plan_t plan, int* K, int* T, double* c, double* E, double*
   if (E) *E = f.E;
   if (delta_max) *delta_max = f.delta_max;
   return FBF_OK;
-}
+} FBF_ABI_CATCH("fbf_plan_info")
 
-int fbf_plan_radius(fbf_plan_t plan, int* r) {
+int fbf_plan_radius(fbf_plan_t plan, int* r) try {
   if (!plan || !r) return fbf::set_error(FBF_EINVAL, "fbf_plan_radius: NULL argument");
   *r = plan->p.r;
   return FBF_OK;
-}
+} FBF_ABI_CATCH("fbf_plan_radius")
 
-int fbf_plan_destroy(fbf_plan_t plan) {
+int fbf_plan_destroy(fbf_plan_t plan) try {
   delete plan;
   return FBF_OK;
-}
+} FBF_ABI_CATCH("fbf_plan_destroy")
 
 int fbf_filter(fbf_plan_t plan, const float* d_in, float* d_out, int H, int W,
-               size_t pitch_elems, void* cuda_stream) {
+               size_t pitch_elems, void* cuda_stream) try {
   if (!plan) return fbf::set_error(FBF_EINVAL, "fbf_filter: plan is NULL");
   if (!d_in || !d_out) return fbf::set_error(FBF_EINVAL, "fbf_filter: NULL image pointer");
   if (H < 1 || W < 1) return fbf::set_error(FBF_EINVAL, "fbf_filter: H and W must be >= 1");
@@ -185,10 +183,10 @@ int fbf_filter(fbf_plan_t plan, const float* d_in, float* d_out, int H, int W,
     default:
       return fbf::set_error(FBF_EINVAL, "fbf_filter: unknown precision form");
   }
-}
+} FBF_ABI_CATCH("fbf_filter")
 
 int fbf_filter_noalloc(fbf_plan_t plan, const float* d_in, float* d_out, int H, int W,
-                       size_t pitch_elems, void* cuda_stream) {
+                       size_t pitch_elems, void* cuda_stream) try {
   if (!plan) return fbf::set_error(FBF_EINVAL, "fbf_filter_noalloc: plan is NULL");
   if (!d_in || !d_out) return fbf::set_error(FBF_EINVAL, "fbf_filter_noalloc: NULL image pointer");
   if (H < 1 || W < 1) return fbf::set_error(FBF_EINVAL, "fbf_filter_noalloc: H and W must be >= 1");
@@ -200,22 +198,22 @@ int fbf_filter_noalloc(fbf_plan_t plan, const float* d_in, float* d_out, int H, 
   if (plan->p.precision != FBF_FP32)
     return fbf::set_error(FBF_EUNSUPPORTED, "fbf_filter_noalloc: only the FBF_FP32 form");
   return fbf::launch_fp32_noalloc(plan->p.dp, d_in, d_out, H, W, pitch_elems, cuda_stream);
-}
+} FBF_ABI_CATCH("fbf_filter_noalloc")
 
 const char* fbf_last_error(void) { return fbf::g_last_error.c_str(); }
 
 const char* fbf_version(void) { return "fbf-gb300 0.1"; }
 
-int fbf_device_errors(int* flags, int clear) {
+int fbf_device_errors(int* flags, int clear) try {
   if (!flags) return fbf::set_error(FBF_EINVAL, "fbf_device_errors: flags is NULL");
   return fbf::device_errors(flags, clear);
-}
+} FBF_ABI_CATCH("fbf_device_errors")
 
 // Test hook: E(K,T) for K = 1..Kc at one T from the C++ fitter (host only).
-int fbf_debug_error_curve(const double* b, int R, int T, int Kc, double* E_out) {
+int fbf_debug_error_curve(const double* b, int R, int T, int Kc, double* E_out) try {
   if (!b || !E_out || R < 1 || T < 1 || Kc < 1) return fbf::set_error(FBF_EINVAL, "bad argument");
   fbf::kernel_error_curve(b, R, T, Kc, E_out);
   return FBF_OK;
-}
+} FBF_ABI_CATCH("fbf_debug_error_curve")
 
 }  // extern "C"

@@ -17,6 +17,7 @@
 // Readings where the paper is silent: T_max = 4R, doubled while the optimum is above
 // T_max/2; errors below 1e-20 ||b||^2 count as equal and the smallest T among them wins.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <thread>
@@ -128,13 +129,30 @@ std::vector<double> error_table(const Folded& F, int T_max, int Kc) {
   unsigned hw = std::thread::hardware_concurrency();
   int nth = (int)std::max(1u, std::min(hw ? hw : 1u, 16u));
   nth = std::min(nth, T_max);
-  std::vector<std::thread> pool;
-  for (int w = 0; w < nth; ++w) {
-    pool.emplace_back([&, w]() {
+  // stripe w takes T = 1 + w, 1 + w + nth, ...; an exception in a stripe (an allocation) is
+  // recorded and rethrown here after every thread has joined
+  std::atomic<bool> failed{false};
+  auto stripe = [&](int w) {
+    try {
       for (int T = 1 + w; T <= T_max; T += nth) reduce(F, T, Kc, &tab[(size_t)(T - 1) * Kc], nullptr);
-    });
+    } catch (...) {
+      failed = true;
+    }
+  };
+  std::vector<std::thread> pool;
+  pool.reserve(nth);
+  int started = 1;
+  for (; started < nth; ++started) {
+    try {
+      pool.emplace_back(stripe, started);
+    } catch (...) {
+      break;                                   // no more threads: this one takes the rest
+    }
   }
+  for (int w = started; w < nth; ++w) stripe(w);
+  stripe(0);
   for (auto& th : pool) th.join();
+  if (failed) throw std::bad_alloc();
   return tab;
 }
 

@@ -95,7 +95,7 @@ int prepare(HostCtx& c, size_t n) {
 }  // namespace
 
 extern "C" int fbf_filter_host(fbf_plan_t plan, const float* host_in, float* host_out, int H, int W,
-                               size_t pitch_elems, void* cuda_stream) {
+                               size_t pitch_elems, void* cuda_stream) try {
   if (!plan) return fbf::set_error(FBF_EINVAL, "fbf_filter_host: plan is NULL");
   if (!host_in || !host_out) return fbf::set_error(FBF_EINVAL, "fbf_filter_host: NULL image pointer");
   if (H < 1 || W < 1) return fbf::set_error(FBF_EINVAL, "fbf_filter_host: H and W must be >= 1");
@@ -227,4 +227,4 @@ extern "C" int fbf_filter_host(fbf_plan_t plan, const float* host_in, float* hos
   e = cudaStreamSynchronize(c->down);
   if (e != cudaSuccess) return drain(fail("synchronise", e));
   return FBF_OK;
-}
+} FBF_ABI_CATCH("fbf_filter_host")

@@ -3,6 +3,8 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <exception>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -70,6 +72,17 @@ const Plan* plan_of(fbf_plan_t h);
 
 // ---- errors ---------------------------------------------------------------------------
 int set_error(int code, const std::string& msg);
+
+// Closes each entry point of the ABI, written as a function-try-block: a C++ exception from
+// the host side (an allocation, a thread that cannot start) becomes FBF_ENOMEM with a
+// message, so that no exception crosses the C ABI.
+#define FBF_ABI_CATCH(fn)                                                                 \
+  catch (const std::bad_alloc&) {                                                         \
+    return fbf::set_error(FBF_ENOMEM, fn ": out of host memory");                         \
+  }                                                                                       \
+  catch (const std::exception& ex) {                                                      \
+    return fbf::set_error(FBF_ENOMEM, std::string(fn ": host resources: ") + ex.what());  \
+  }
 void clear_error();
 
 // ---- kernels --------------------------------------------------------------------------

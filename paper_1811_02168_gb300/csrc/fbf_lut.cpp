@@ -48,7 +48,7 @@ bool inside(const std::vector<double>& g, double x) {
 
 extern "C" {
 
-int fbf_lut_build(fbf_lut_t* out, int R, const double* sigmas, int n_sigma, const double* eps, int n_eps) {
+int fbf_lut_build(fbf_lut_t* out, int R, const double* sigmas, int n_sigma, const double* eps, int n_eps) try {
   if (!out) return fbf::set_error(FBF_EINVAL, "fbf_lut_build: out is NULL");
   *out = nullptr;
   if (!sigmas || !eps) return fbf::set_error(FBF_EINVAL, "fbf_lut_build: NULL grid");
@@ -88,9 +88,9 @@ int fbf_lut_build(fbf_lut_t* out, int R, const double* sigmas, int n_sigma, cons
   *out = L;
   fbf::clear_error();
   return FBF_OK;
-}
+} FBF_ABI_CATCH("fbf_lut_build")
 
-int fbf_lut_entry(fbf_lut_t lut, int i_sigma, int j_eps, int* K, int* T) {
+int fbf_lut_entry(fbf_lut_t lut, int i_sigma, int j_eps, int* K, int* T) try {
   if (!lut || !K || !T) return fbf::set_error(FBF_EINVAL, "fbf_lut_entry: NULL argument");
   const int ns = (int)lut->sigma.size(), nu = (int)lut->u.size();
   if (i_sigma < 0 || i_sigma >= ns || j_eps < 0 || j_eps >= nu)
@@ -98,9 +98,9 @@ int fbf_lut_entry(fbf_lut_t lut, int i_sigma, int j_eps, int* K, int* T) {
   *K = lut->K[(size_t)i_sigma * nu + j_eps];
   *T = lut->T[(size_t)i_sigma * nu + j_eps];
   return FBF_OK;
-}
+} FBF_ABI_CATCH("fbf_lut_entry")
 
-int fbf_lut_lookup(fbf_lut_t lut, double sigma, double eps, int* K, int* T) {
+int fbf_lut_lookup(fbf_lut_t lut, double sigma, double eps, int* K, int* T) try {
   if (!lut || !K || !T) return fbf::set_error(FBF_EINVAL, "fbf_lut_lookup: NULL argument");
   if (!(sigma > 0) || !(eps > 0) || !(eps < 1)) return fbf::set_error(FBF_EINVAL, "fbf_lut_lookup: sigma > 0, 0 < eps < 1");
   const double u = std::log(1.0 / eps);
@@ -122,9 +122,9 @@ int fbf_lut_lookup(fbf_lut_t lut, double sigma, double eps, int* K, int* T) {
   *K = std::max(1, (int)std::lround(bil(lut->K)));
   *T = std::max(1, (int)std::lround(bil(lut->T)));
   return FBF_OK;
-}
+} FBF_ABI_CATCH("fbf_lut_lookup")
 
-int fbf_plan_from_lut(fbf_plan_t* out, fbf_lut_t lut, double sigma, double eps, double theta, int precision) {
+int fbf_plan_from_lut(fbf_plan_t* out, fbf_lut_t lut, double sigma, double eps, double theta, int precision) try {
   if (!out) return fbf::set_error(FBF_EINVAL, "fbf_plan_from_lut: out is NULL");
   *out = nullptr;
   int K = 0, T = 0;
@@ -134,9 +134,9 @@ int fbf_plan_from_lut(fbf_plan_t* out, fbf_lut_t lut, double sigma, double eps, 
   std::vector<double> b(2 * R + 1);
   for (int t = -R; t <= R; ++t) b[t + R] = std::exp(-(double)t * t / (2.0 * sigma * sigma));
   return fbf::build_plan(out, b.data(), R, theta, K, 0.0, precision, 0, sigma, T);
-}
+} FBF_ABI_CATCH("fbf_plan_from_lut")
 
-int fbf_lut_save(fbf_lut_t lut, const char* path) {
+int fbf_lut_save(fbf_lut_t lut, const char* path) try {
   if (!lut || !path) return fbf::set_error(FBF_EINVAL, "fbf_lut_save: NULL argument");
   FILE* f = std::fopen(path, "w");
   if (!f) return fbf::set_error(FBF_EINVAL, std::string("fbf_lut_save: cannot open ") + path);
@@ -147,16 +147,17 @@ int fbf_lut_save(fbf_lut_t lut, const char* path) {
   for (int i = 0; i < ns * nu; ++i) std::fprintf(f, "%d %d\n", lut->K[i], lut->T[i]);
   const bool ok = std::fclose(f) == 0;
   return ok ? FBF_OK : fbf::set_error(FBF_EINVAL, "fbf_lut_save: write failed");
-}
+} FBF_ABI_CATCH("fbf_lut_save")
 
-int fbf_lut_load(fbf_lut_t* out, const char* path) {
+int fbf_lut_load(fbf_lut_t* out, const char* path) try {
   if (!out || !path) return fbf::set_error(FBF_EINVAL, "fbf_lut_load: NULL argument");
   *out = nullptr;
   FILE* f = std::fopen(path, "r");
   if (!f) return fbf::set_error(FBF_EINVAL, std::string("fbf_lut_load: cannot open ") + path);
   int ver = 0, R = 0, ns = 0, nu = 0;
-  bool ok = std::fscanf(f, "fbf-lut %d %d %d %d", &ver, &R, &ns, &nu) == 4 && ver == 1 && R >= 1 && ns >= 2 &&
-            nu >= 2 && ns <= 4096 && nu <= 4096;
+  // the same bounds as fbf_lut_build: the file is input, and R sizes the samples of a plan
+  bool ok = std::fscanf(f, "fbf-lut %d %d %d %d", &ver, &R, &ns, &nu) == 4 && ver == 1 && R >= 1 &&
+            R <= (1 << 16) && ns >= 2 && nu >= 2 && ns <= 4096 && nu <= 4096;
   fbf_lut_s* L = ok ? new (std::nothrow) fbf_lut_s() : nullptr;
   if (ok && !L) { std::fclose(f); return fbf::set_error(FBF_ENOMEM, "fbf_lut_load: out of host memory"); }
   if (ok) {
@@ -165,7 +166,7 @@ int fbf_lut_load(fbf_lut_t* out, const char* path) {
     L->u.resize(nu);
     L->K.resize((size_t)ns * nu);
     L->T.resize((size_t)ns * nu);
-    for (int i = 0; ok && i < ns; ++i) ok = std::fscanf(f, "%lf", &L->sigma[i]) == 1;
+    for (int i = 0; ok && i < ns; ++i) ok = std::fscanf(f, "%lf", &L->sigma[i]) == 1 && L->sigma[i] > 0;
     for (int j = 0; ok && j < nu; ++j) {
       double e = 0;
       ok = std::fscanf(f, "%lf", &e) == 1 && e > 0 && e < 1;
@@ -181,11 +182,11 @@ int fbf_lut_load(fbf_lut_t* out, const char* path) {
   *out = L;
   fbf::clear_error();
   return FBF_OK;
-}
+} FBF_ABI_CATCH("fbf_lut_load")
 
-int fbf_lut_destroy(fbf_lut_t lut) {
+int fbf_lut_destroy(fbf_lut_t lut) try {
   delete lut;
   return FBF_OK;
-}
+} FBF_ABI_CATCH("fbf_lut_destroy")
 
 }  // extern "C"

@@ -320,7 +320,7 @@ void percentiles(std::vector<double> xs, double* p50, double* p99) {
 extern "C" {
 
 int fbf_server_create(fbf_server_t* out, int device, int precision, uint64_t hbm_budget_bytes,
-                      int max_batch, int max_inflight) {
+                      int max_batch, int max_inflight) try {
   if (!out) return fbf::set_error(FBF_EINVAL, "fbf_server_create: out is NULL");
   *out = nullptr;
   if (precision != FBF_FP32 && precision != FBF_FP16_TC && precision != FBF_BF16_TC)
@@ -368,10 +368,10 @@ int fbf_server_create(fbf_server_t* out, int device, int precision, uint64_t hbm
   s->worker = std::thread(worker_main, s);
   *out = s;
   return FBF_OK;
-}
+} FBF_ABI_CATCH("fbf_server_create")
 
 int fbf_server_submit(fbf_server_t s, const float* host_in, float* host_out, int H, int W, double theta,
-                      double sigma, int R, int K, double eps, fbf_ticket_t* ticket) {
+                      double sigma, int R, int K, double eps, fbf_ticket_t* ticket) try {
   if (!s || !host_in || !host_out) return fbf::set_error(FBF_EINVAL, "fbf_server_submit: NULL argument");
   if (H < 1 || W < 1) return fbf::set_error(FBF_EINVAL, "fbf_server_submit: H and W must be >= 1");
   const uint64_t bytes = 8ull * (uint64_t)H * (uint64_t)W;
@@ -403,12 +403,12 @@ int fbf_server_submit(fbf_server_t s, const float* host_in, float* host_out, int
   }
   s->work.notify_one();
   return FBF_OK;
-}
+} FBF_ABI_CATCH("fbf_server_submit")
 
 int fbf_server_replay(fbf_server_t s, int n, const double* arrival_s, const float* const* host_in,
                       float* const* host_out, const int* H, const int* W, const double* theta,
                       const double* sigma, const int* R, const int* K, const double* eps,
-                      fbf_ticket_t* tickets) {
+                      fbf_ticket_t* tickets) try {
   if (!s || n < 0 || (n > 0 && (!arrival_s || !host_in || !host_out || !H || !W || !theta || !sigma || !R ||
                                 !K || !eps)))
     return fbf::set_error(FBF_EINVAL, "fbf_server_replay: NULL argument");
@@ -433,27 +433,27 @@ int fbf_server_replay(fbf_server_t s, int n, const double* arrival_s, const floa
     if (rc != FBF_OK) return rc;
   }
   return FBF_OK;
-}
+} FBF_ABI_CATCH("fbf_server_replay")
 
-int fbf_server_poll(fbf_server_t s, fbf_ticket_t ticket, int* status) {
+int fbf_server_poll(fbf_server_t s, fbf_ticket_t ticket, int* status) try {
   if (!s || !status) return fbf::set_error(FBF_EINVAL, "fbf_server_poll: NULL argument");
   std::lock_guard<std::mutex> g(s->mu);
   auto it = s->status.find(ticket);
   if (it == s->status.end()) return fbf::set_error(FBF_EINVAL, "fbf_server_poll: unknown ticket");
   *status = it->second;
   return FBF_OK;
-}
+} FBF_ABI_CATCH("fbf_server_poll")
 
-int fbf_server_drain(fbf_server_t s, double timeout_s) {
+int fbf_server_drain(fbf_server_t s, double timeout_s) try {
   if (!s) return fbf::set_error(FBF_EINVAL, "fbf_server_drain: NULL server");
   std::unique_lock<std::mutex> lk(s->mu);
   const bool ok = s->idle.wait_for(lk, std::chrono::duration<double>(timeout_s < 0 ? 0 : timeout_s),
                                    [s] { return s->pending == 0; });
   if (!ok) return fbf::set_error(FBF_ETIMEDOUT, "fbf_server_drain: requests still pending");
   return FBF_OK;
-}
+} FBF_ABI_CATCH("fbf_server_drain")
 
-int fbf_server_stats(fbf_server_t s, fbf_server_stats_t* out) {
+int fbf_server_stats(fbf_server_t s, fbf_server_stats_t* out) try {
   if (!s || !out) return fbf::set_error(FBF_EINVAL, "fbf_server_stats: NULL argument");
   std::vector<std::array<double, 6>> tr;
   {
@@ -494,9 +494,9 @@ int fbf_server_stats(fbf_server_t s, fbf_server_stats_t* out) {
     out->tail_batch = t.batch / t.n;
   }
   return FBF_OK;
-}
+} FBF_ABI_CATCH("fbf_server_stats")
 
-int fbf_server_reset_stats(fbf_server_t s) {
+int fbf_server_reset_stats(fbf_server_t s) try {
   if (!s) return fbf::set_error(FBF_EINVAL, "fbf_server_reset_stats: NULL server");
   std::lock_guard<std::mutex> g(s->mu);
   if (s->pending != 0) return fbf::set_error(FBF_EBUSY, "fbf_server_reset_stats: requests pending");
@@ -506,9 +506,9 @@ int fbf_server_reset_stats(fbf_server_t s) {
   s->t_first = s->t_last = -1;
   s->trace.clear();
   return FBF_OK;
-}
+} FBF_ABI_CATCH("fbf_server_reset_stats")
 
-int fbf_server_destroy(fbf_server_t s) {
+int fbf_server_destroy(fbf_server_t s) try {
   if (!s) return FBF_OK;
   {
     std::lock_guard<std::mutex> g(s->mu);
@@ -528,6 +528,6 @@ int fbf_server_destroy(fbf_server_t s) {
   cudaSetDevice(cur);
   delete s;
   return FBF_OK;
-}
+} FBF_ABI_CATCH("fbf_server_destroy")
 
 }  // extern "C"

@@ -88,10 +88,17 @@ def test_save_load_and_errors(lut, tmp_path):
             assert back.entry(i, j) == lut.entry(i, j)
     assert back.lookup(42.0, 0.02) == lut.lookup(42.0, 0.02)
     bad = tmp_path / "bad.lut"
-    bad.write_text("fbf-lut 1\n255 2 2\n10\n")
-    with pytest.raises(B.FbfError) as ei:
-        B.Lut(path=str(bad))
-    assert ei.value.code == B.FBF_EINVAL
+    for text in ("fbf-lut 1\n255 2 2\n10\n",                                     # truncated
+                 "fbf-lut 1\n2147483647 2 2\n10\n20\n0.1\n0.01\n1 1\n1 1\n1 1\n1 1\n",  # R too large
+                 "fbf-lut 1\n255 2 2\n-10\n20\n0.1\n0.01\n1 1\n1 1\n1 1\n1 1\n",       # sigma <= 0
+                 "fbf-lut 1\n255 2 2\n10\n20\n0.1\n0.01\n1 1\n0 1\n1 1\n1 1\n"):       # K = 0
+        bad.write_text(text)
+        with pytest.raises(B.FbfError) as ei:
+            B.Lut(path=str(bad))
+        assert ei.value.code == B.FBF_EINVAL
+    good = "fbf-lut 1\n255 2 2\n10\n20\n0.1\n0.01\n1 1\n1 1\n1 1\n1 1\n"
+    bad.write_text(good)
+    assert B.Lut(path=str(bad)).entry(1, 1) == (1, 1)
     with pytest.raises(B.FbfError) as ei:
         lut.lookup(5.0, 0.01)                      # sigma below the grid
     assert ei.value.code == B.FBF_EUNSUPPORTED
