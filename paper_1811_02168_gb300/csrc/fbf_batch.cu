@@ -160,7 +160,7 @@ DeviceParams padded(const DeviceParams& dp, int rad) {
 
 // ---- autotuner cache ----------------------------------------------------------------------
 std::mutex g_tune_mu;
-std::map<std::string, int> g_tune;   // key -> candidate index
+std::map<std::string, std::string> g_tune;   // key -> candidate name
 bool g_tune_loaded = false;
 
 std::string tune_key(int dev, int cls, long long pixels, int kmax) {
@@ -182,14 +182,11 @@ void tune_load_locked() {
   if (!path) return;
   FILE* f = std::fopen(path, "r");
   if (!f) return;
-  char key[256], cfg[128];
-  while (std::fscanf(f, "%255s %127s", key, cfg) == 2) {
-    std::string k(key);
-    // find the class index from the key's radius and the candidate by name
-    for (size_t ci = 0; ci < classes().size(); ++ci)
-      for (size_t j = 0; j < classes()[ci].cands.size(); ++j)
-        if (std::string(classes()[ci].cands[j].name) == cfg) g_tune[k] = (int)j;
-  }
+  // one "key name" pair per line; other lines are ignored, later lines win, and a name is
+  // resolved within the key's own class when it is used
+  char line[512], key[256], cfg[128], extra[2];
+  while (std::fgets(line, sizeof(line), f))
+    if (std::sscanf(line, "%255s %127s %1s", key, cfg, extra) == 2) g_tune[key] = cfg;
   std::fclose(f);
 }
 
@@ -421,7 +418,8 @@ int prepare(Batch* b, std::vector<ClassPlan>* cps, size_t* list_bytes, cudaStrea
         std::lock_guard<std::mutex> lk(g_tune_mu);
         tune_load_locked();
         auto it = g_tune.find(key);
-        if (it != g_tune.end() && it->second < (int)cands.size()) cached = it->second;
+        for (size_t j = 0; it != g_tune.end() && j < cands.size(); ++j)
+          if (it->second == cands[j].name) cached = (int)j;
       }
       if (cached >= 0) {
         choice = cached;
@@ -438,9 +436,13 @@ int prepare(Batch* b, std::vector<ClassPlan>* cps, size_t* list_bytes, cudaStrea
           if (rc != FBF_OK) return rc;
           std::vector<ClassPlan> v{one};
           write_lists(b, v);
-          cudaEvent_t e0, e1;
-          cudaEventCreate(&e0);
-          cudaEventCreate(&e1);
+          cudaEvent_t e0 = nullptr, e1 = nullptr;
+          cudaError_t ee = cudaEventCreate(&e0);
+          if (ee == cudaSuccess) ee = cudaEventCreate(&e1);
+          if (ee != cudaSuccess) {
+            if (e0) cudaEventDestroy(e0);
+            return set_error(FBF_ECUDA, std::string("fbf_batch: autotune: ") + cudaGetErrorString(ee));
+          }
           float ms_best = 1e30f;
           for (int rep = 0; rep < 3; ++rep) {
             cudaEventRecord(e0, st);
@@ -458,7 +460,7 @@ int prepare(Batch* b, std::vector<ClassPlan>* cps, size_t* list_bytes, cudaStrea
           if (ms_best < best) { best = ms_best; choice = (int)j; }
         }
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tune[key] = choice;
+        g_tune[key] = cands[choice].name;
         tune_store_locked(key, cands[choice].name);
       }
     }

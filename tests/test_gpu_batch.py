@@ -194,3 +194,70 @@ def test_tensor_core_batch_graph_replay(B):
         for plan, x, y, H, W in items:
             assert _close(y, _single(B, plan, x))
     batch.close()
+
+
+_TUNE_CHILD = r'''
+import json, sys
+import torch
+sys.path.insert(0, sys.argv[1])
+from paper_1811_02168_gb300 import binding as B
+from paper_1811_02168_gb300.synth import voronoi_image
+B.lib()
+batch = B.Batch(8, autotune=True)
+ys, refs = [], []
+for theta, (H, W) in zip((2.0, 5.0, 10.0), [(300, 260), (500, 333), (700, 410)]):   # r = 6, 15, 30
+    plan = B.Plan(30.0, 255, theta, K=5)
+    x = torch.from_numpy(voronoi_image(H, W, 10, 30.0, 10.0, seed=H)).cuda()
+    ref = torch.empty_like(x)
+    B.fbf_filter(plan.handle, x.data_ptr(), ref.data_ptr(), H, W, W, torch.cuda.current_stream().cuda_stream)
+    y = torch.full_like(x, -5.0)
+    batch.submit(plan, x, y)
+    ys.append(y)
+    refs.append(ref)
+batch.launch()
+torch.cuda.synchronize()
+print(json.dumps({"err": max(float((y - r).abs().max()) for y, r in zip(ys, refs)),
+                  "device_errors": B.fbf_device_errors(True)}))
+batch.close()
+'''
+
+
+def test_autotune_cache_file(B, tmp_path):
+    """FBF_TUNE_CACHE: a first process tunes the radius classes with more than one candidate
+    (r = 6, 15, 30) and appends one "key name" line per class, naming a candidate of that
+    class; a second process reads the file back (with a junk line, a three-token line and a
+    key paired with another class's candidate, all ignored; the last makes that class tune
+    again) and filters the same images.  Both match fbf_filter within the FP32 tolerance."""
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    child = tmp_path / "child.py"
+    child.write_text(_TUNE_CHILD)
+    cache = tmp_path / "tune.txt"
+    env = dict(os.environ, FBF_TUNE_CACHE=str(cache))
+
+    def run():
+        out = subprocess.run([sys.executable, str(child), root], env=env, capture_output=True, text=True,
+                             timeout=600)
+        assert out.returncode == 0, out.stderr[-2000:]
+        res = json.loads(out.stdout.strip().splitlines()[-1])
+        assert res["device_errors"] == 0
+        assert res["err"] <= TOL
+        return res
+
+    run()
+    lines = cache.read_text().split("\n")
+    pairs = [ln.split() for ln in lines if ln.strip()]
+    assert len(pairs) == 3 and all(len(p) == 2 for p in pairs)
+    for rad, (key, name) in zip((6, 15, 30), sorted(pairs, key=lambda p: int(p[0].split("/r")[1].split("/")[0]))):
+        assert f"/r{rad}/" in key and name.startswith(f"r{rad}_ty")
+    key15 = next(k for k, _ in pairs if "/r15/" in k)
+    # the last line for key15 names a candidate of another class: it wins the file's
+    # pairing but is ignored when used, so r = 15 is tuned again and a new line appended
+    cache.write_text("junk\n" + f"{key15} r15_ty96_nt512 extra\n" + "\n".join(p[0] + " " + p[1] for p in pairs) +
+                     f"\n{key15} r6_ty112_nt512\n")
+    run()
+    last = cache.read_text().strip().split("\n")[-1].split()
+    assert last[0] == key15 and last[1].startswith("r15_ty")
