@@ -42,6 +42,21 @@ def test_exports_every_declared_symbol():
     assert set(names) <= set(B.SIGNATURES), "binding lacks a mirror for a declared symbol"
 
 
+def test_binding_constants_equal_the_header():
+    """Every integer constant the binding mirrors has the header's value (error codes,
+    statuses, precision forms, flags, limits)."""
+    defined = {}
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        for m in re.finditer(r"^#define\s+(FBF_\w+)\s+\(?(\d+)u?(?:\s*<<\s*(\d+))?\)?", open(h).read(), flags=re.M):
+            defined[m.group(1)] = int(m.group(2)) << int(m.group(3) or 0)
+    mirrored = {n: getattr(B, n) for n in dir(B) if n.startswith("FBF_") and isinstance(getattr(B, n), int)}
+    assert {"FBF_OK", "FBF_EINVAL", "FBF_EUNSUPPORTED", "FBF_FP32", "FBF_BF16_TC", "FBF_MAX_K"} <= set(mirrored)
+    unknown = sorted(set(mirrored) - set(defined))
+    assert not unknown, f"binding constants the header does not define: {unknown}"
+    wrong = {n: (v, defined[n]) for n, v in mirrored.items() if defined[n] != v}
+    assert not wrong, wrong
+
+
 def _phi_hat(c, T, R):
     t = np.arange(-R, R + 1)
     return ofit.phi_hat(t, c, T)
