@@ -14,7 +14,10 @@ Requests (an image plus theta, sigma and K) arrive over time.  The loop:
     on the GPU -- requests that arrive while others run join the next launch instead of
     waiting for a fixed batch to fill (continuous batching);
   * copies results back (download stream, after the launch) and, when a launch's results are on
-    the host, records each request's latency (completion - arrival) and frees its budget.
+    the host, records each request's latency (completion - arrival) and frees its budget;
+  * a backend error (an upload, a launch, a completion query) fails only the requests it
+    concerns: they are counted as failed, their budget and device state are released, and
+    the loop goes on with the others.
 
 Plans (the fitted K, T, c per (theta, sigma, K)) are cached, so the FP64 fit runs once per
 parameter set.  The device work is the library's batched path (``binding.Batch``); the
@@ -44,6 +47,7 @@ class Request:
     launched: float = math.nan
     done: float = math.nan
     dev: object = None        # backend state
+    error: str = ""           # why the request failed ("" if it did not)
 
     @property
     def nbytes(self) -> int:
@@ -67,6 +71,7 @@ class ServeStats:
     max_inflight_seen: int = 0
     hbm_high_water: int = 0
     waited_for_budget: int = 0
+    failed: int = 0
 
     def pct(self, q: float) -> float:
         if not self.latencies:
@@ -81,7 +86,7 @@ class ServeStats:
                 "p50_ms": 1e3 * self.pct(50), "p99_ms": 1e3 * self.pct(99),
                 "launches": self.launches, "max_inflight": self.max_inflight_seen,
                 "hbm_high_water_bytes": self.hbm_high_water,
-                "waited_for_budget": self.waited_for_budget,
+                "waited_for_budget": self.waited_for_budget, "failed": self.failed,
                 "slowest_1pct": self.tail_breakdown(99)}
 
     def tail_breakdown(self, q: float) -> dict:
@@ -120,6 +125,16 @@ class Server:
         used = 0
         i = 0
         t0 = clock()
+
+        def fail(rs, err, release=True):
+            nonlocal used
+            for r in rs:
+                r.error = f"{type(err).__name__}: {err}"
+                st.failed += 1
+                used -= r.nbytes
+                if release:
+                    self.be.release(r)
+
         while i < len(reqs) or waiting or admitted or inflight:
             now = clock() - t0
             busy = False
@@ -136,23 +151,37 @@ class Server:
                 used += r.nbytes
                 st.hbm_high_water = max(st.hbm_high_water, used)
                 r.admitted = now
-                self.be.admit(r)
-                admitted.append(r)
+                try:
+                    self.be.admit(r)
+                except Exception as e:       # the backend cleaned up; nothing to release
+                    fail([r], e, release=False)
+                else:
+                    admitted.append(r)
                 busy = True
             # continuous batching: launch what is admitted whenever a launch slot is free
             if admitted and len(inflight) < self.max_inflight:
                 for r in admitted:
                     r.launched = now
-                h = self.be.launch(admitted)
-                inflight.append((h, admitted))
-                st.launches += 1
-                st.max_inflight_seen = max(st.max_inflight_seen, len(inflight))
+                try:
+                    h = self.be.launch(admitted)
+                except Exception as e:
+                    fail(admitted, e)
+                else:
+                    inflight.append((h, admitted))
+                    st.launches += 1
+                    st.max_inflight_seen = max(st.max_inflight_seen, len(inflight))
                 admitted = []
                 busy = True
             # completions (results on the host)
             still = []
             for h, rs in inflight:
-                if self.be.done(h):
+                try:
+                    finished = self.be.done(h)
+                except Exception as e:
+                    fail(rs, e)
+                    busy = True
+                    continue
+                if finished:
                     t = clock() - t0
                     for r in rs:
                         r.done = t
@@ -211,6 +240,18 @@ class TorchBackend:
         r.dev = (x, y, ev)
 
     def launch(self, rs: list[Request]):
+        try:
+            return self._launch(rs)
+        except Exception:
+            # wait for what was queued; images left in the batch's queue (a submit that
+            # failed before the launch) must not run with the next launch: a new batch
+            self.torch.cuda.synchronize(self.dev)
+            if self.batch.pending() > 0:
+                self.batch.close()
+                self.batch = self.B.Batch(4096)
+            raise
+
+    def _launch(self, rs: list[Request]):
         torch = self.torch
         for r in rs:
             x, y, ev = r.dev

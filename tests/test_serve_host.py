@@ -62,3 +62,53 @@ def test_request_larger_than_the_budget_is_refused():
     r = Request(0, 0.0, 1000, 1000, 2.0, 30.0, 4)
     with pytest.raises(ValueError):
         Server(FakeBackend(), hbm_budget_bytes=1000).run([r])
+
+
+class _FailingBackend(FakeBackend):
+    """FakeBackend whose admit of chosen requests, chosen launches (by index) and completion
+    queries of chosen launches raise, as a failing device call would."""
+
+    def __init__(self, bad_admit=(), bad_launch=(), bad_done=(), **kw):
+        super().__init__(**kw)
+        self.bad_admit, self.bad_launch, self.bad_done = set(bad_admit), set(bad_launch), set(bad_done)
+        self.n_launch = 0
+        self.handles = {}
+
+    def admit(self, r):
+        if r.rid in self.bad_admit:
+            raise RuntimeError("upload failed")
+        super().admit(r)
+
+    def launch(self, rs):
+        n = self.n_launch
+        self.n_launch += 1
+        if n in self.bad_launch:
+            raise RuntimeError("launch failed")
+        h = super().launch(rs)
+        self.handles[n] = h
+        return (n, h)
+
+    def done(self, h):
+        n, t = h
+        if n in self.bad_done:
+            raise RuntimeError("completion query failed")
+        return super().done(t)
+
+
+def test_backend_failures_fail_only_their_requests():
+    """An upload, a launch and a completion query that fail (errors raised by a fake of the
+    failing call, on the host) fail exactly the requests they concern; every other request
+    completes, the failed ones release their budget and device state, and the loop ends."""
+    reqs = _requests(60, rate=20000.0, seed=9)
+    be = _FailingBackend(bad_admit={3, 17}, bad_launch={1}, bad_done={2}, sec_per_pixel=2e-9)
+    st = Server(be, hbm_budget_bytes=1 << 30, max_batch=8).run(reqs)
+    failed = [r for r in reqs if r.error]
+    assert st.failed == len(failed) and st.requests + st.failed == len(reqs)
+    assert {3, 17} <= {r.rid for r in failed}
+    assert {r.rid for r in failed if "upload" in r.error} == {3, 17}
+    assert any("launch failed" in r.error for r in failed)
+    assert any("completion query failed" in r.error for r in failed)
+    assert all(r.done == r.done for r in reqs if not r.error)        # served: a completion time
+    assert all(r.done != r.done for r in failed)                       # failed: none (NaN)
+    assert be.live_bytes == 0                                          # all device state released
+    assert st.summary()["failed"] == len(failed)
