@@ -14,7 +14,8 @@
  *
  * Conventions for every entry point:
  *   - Return value: FBF_OK (0) or one of the FBF_E* codes below.  No C++ exception
- *     crosses this boundary.  fbf_last_error() gives a message for the calling thread.
+ *     crosses this boundary: a host allocation or a thread that cannot start inside a call
+ *     returns FBF_ENOMEM.  fbf_last_error() gives a message for the calling thread.
  *   - Images are single-channel float32, row-major, values in [0, R].  Integer values
  *     (8-bit images converted to float) are the case the paper treats (Lambda holds only
  *     integers, Section II); other values are filtered with the same formula.
