@@ -405,10 +405,12 @@ class Plan:
 def bilateral_filter(plan: Plan, image, out=None, stream=None):
     """f_BF of one 2-D float32 image.
 
-    ``image`` is a torch tensor.  On the GPU it is filtered in place of memory on the
-    current (or given) stream and a device tensor is returned.  On the host it goes through
-    ``fbf_filter_host`` (uploads, band-wise filter and downloads overlapped; returns when the
-    result is on the host): the end-to-end path.
+    ``image`` is a torch tensor.  On the GPU it is filtered in device memory on the current
+    (or given) stream, asynchronously, into ``out`` or a new device tensor, which is
+    returned.  On the host it goes through ``fbf_filter_host``, the end-to-end path: the image
+    is taken page-locked (copied into pinned memory if it is not) and the result is a pinned
+    tensor, so the kernel reads and writes host memory directly; returns when the result is
+    on the host.
     """
     import torch
     if image.dim() != 2 or image.dtype != torch.float32:
