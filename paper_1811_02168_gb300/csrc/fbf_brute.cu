@@ -134,7 +134,7 @@ int launch(const Params& p, cudaStream_t st) {
   cudaError_t e = cudaFuncSetAttribute(fbf_brute_kernel<RAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return set_error(FBF_ECUDA, std::string("fbf_brute_filter: ") + cudaGetErrorString(e));
   Params q = p;
-  const dim3 grid((unsigned)((p.W + BX - 1) / BX), (unsigned)((p.H + BY - 1) / BY));
+  const dim3 grid((unsigned)(((long long)p.W + BX - 1) / BX), (unsigned)(((long long)p.H + BY - 1) / BY));
   fbf_brute_kernel<RAD><<<grid, NT, smem, st>>>(q);
   e = cudaGetLastError();
   if (e != cudaSuccess) return set_error(FBF_ECUDA, std::string("fbf_brute_filter: launch: ") + cudaGetErrorString(e));
@@ -153,6 +153,10 @@ extern "C" int fbf_brute_filter(const float* d_in, float* d_out, int H, int W, s
   if (!(theta > 0.0) || !(sigma > 0.0) || !std::isfinite(theta) || !std::isfinite(sigma))
     return set_error(FBF_EINVAL, "fbf_brute_filter: theta and sigma must be positive and finite");
   if (R < 1) return set_error(FBF_EINVAL, "fbf_brute_filter: R must be >= 1");
+  // one launch covers the image with a 2-D grid of 32 x 32 tiles; grid y is at most 65535
+  if (((long long)H + brute::BY - 1) / brute::BY > 65535)
+    return set_error(FBF_EUNSUPPORTED, "fbf_brute_filter: H above " + std::to_string(65535LL * brute::BY) +
+                                           " rows");
   const size_t span = ((size_t)(H - 1) * pitch_elems + (size_t)W) * sizeof(float);
   const char* a = (const char*)d_in;
   const char* o = (const char*)d_out;

@@ -245,6 +245,9 @@ def test_brute_filter_argument_errors():
     assert L.fbf_brute_filter(x, y, 4, 4, 4, 2.0, 30.0, 0, None) == B.FBF_EINVAL
     assert L.fbf_brute_filter(x, x, 4, 4, 4, 2.0, 30.0, 255, None) == B.FBF_EINVAL   # overlap
     assert L.fbf_brute_filter(x, y, 4, 4, 4, 17.0, 30.0, 255, None) == B.FBF_EUNSUPPORTED   # r = 51
+    far = ctypes.c_void_p(1 << 40)
+    H = 65535 * 32 + 1                                                   # grid y above 65535
+    assert L.fbf_brute_filter(x, far, H, 1, 1, 2.0, 30.0, 255, None) == B.FBF_EUNSUPPORTED
 
 def test_server_argument_errors():
     """fbf_server_create rejects bad arguments before touching a device; the other entry
