@@ -189,12 +189,18 @@ def test_deterministic_and_side_stream(B):
 
 
 def test_host_end_to_end_api(B):
-    """bilateral_filter with a host tensor copies in, filters and copies back."""
+    """bilateral_filter: a host tensor takes the end-to-end call (page-locked, filtered by
+    the kernel in host memory, returned on the host), a device tensor the device call; both
+    give fbf_filter's bits."""
     img = voronoi_image(120, 140, 10, 30.0, 10.0, seed=4)
     plan = B.Plan(30.0, 255, 3.0, K=4)
+    ref = _gpu(B, plan, img)
     res = B.bilateral_filter(plan, torch.from_numpy(img))
     assert not res.is_cuda
-    assert np.array_equal(res.numpy(), _gpu(B, plan, img))
+    assert np.array_equal(res.numpy(), ref)
+    dev = B.bilateral_filter(plan, torch.from_numpy(img).cuda())
+    assert dev.is_cuda
+    assert np.array_equal(dev.cpu().numpy(), ref)
 
 
 def test_non_integer_input_uses_the_general_phase_path(B):
