@@ -2,14 +2,17 @@
 """Benchmark: Mpix/s of Fourier bilateral filtering on one GB300 at a stated error against
 the FP64 oracle.
 
-Default workload (the sigma sweep): one 1024 x 1024 synthetic 8-bit image (Voronoi mosaic,
-200 cells, ramp 40, noise 10, seed 1000), theta = 5 (31 x 31 window), sigma in
-{10, 30, 80}, K chosen by Algorithm 1 at eps = 0.01, FP32 form.  One step filters the
-image once per sigma (3 launches, 3.15 Mpix).  Inputs are resident in HBM; L2 is flushed
-(256 MiB write) before every timed step, outside the timed region.  The end-to-end figure
-(`e2e`) runs the same steps from pinned host tensors through the C ABI's host-buffer call,
-wall clock.  The CPU baseline is the FP64 oracle as it stands, in row bands on every host
-core.
+Default workload (the large precision-form image): one 4096 x 4096 synthetic 8-bit image
+(Voronoi mosaic, 2000 cells, ramp 60, noise 15, seed 2000), theta = 10 (61 x 61 window),
+sigma = 10, K = 16 with T optimised, FP32 form; one step filters it once (one launch,
+16.8 Mpix).  Inputs are resident in HBM; L2 is flushed (256 MiB write) before every timed
+step, outside the timed region.  The roofline is the FP32 FMA pipe at the rate the
+library's multiply-add probe measures on the same GPU.  The end-to-end figure (`e2e`) runs
+the same steps from pinned host tensors through the C ABI's host-buffer call, wall clock.
+The CPU baseline is the FP64 oracle as it stands, in row bands on every host core, over
+every pixel; the same oracle output gives the error of every form.  The sigma sweep (one
+1024 x 1024 image, theta 5, sigma 10 / 30 / 80, K from eps 0.01) is measured in the same run
+and reported under "sigma_sweep".
 
 Output: one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle instead
 (the same sharding, a bounded sample per step) with the same metric and config.
@@ -42,7 +45,11 @@ def _args():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["sigma_sweep", "small", "large", "batch", "serve", "psnr"],
-                    default="sigma_sweep")
+                    default="large")
+    ap.add_argument("--no-sweep", action="store_true",
+                    help="skip the sigma-sweep key of the single-image line")
+    ap.add_argument("--ref-seconds", type=float, default=90.0,
+                    help="reference arm: CPU seconds the whole --steps/--warmup run may take")
     ap.add_argument("--serve-seconds", type=float, default=10.0,
                     help="length of the Poisson request stream for --workload serve")
     ap.add_argument("--serve-rate", type=float, default=500.0)
@@ -186,12 +193,20 @@ def _traffic_for(kernel: str):
     return None
 
 
-def _fp32_kernel_name(plans, jobs) -> str:
+def _fp32_kernel_name(plans, jobs, sm_count: int = 152) -> str:
     """The FP32 instantiation fbf_filter runs: f staged by TMA for radii <= 15 when the rows
-    are 16-byte aligned (the bench's tensors are contiguous and freshly allocated), else plain
-    loads.  Both are one source (fbf_fp32_body.cuh); DRAM traffic is recorded per family."""
+    are 16-byte aligned (the bench's tensors are contiguous and freshly allocated); for radii
+    above 15 the carried-row kernel when the image has at least three tiles per CTA (one CTA
+    per SM; tiles 32 wide, 128 rows high up to r = 30, else 64), else plain loads.  All are
+    one source (fbf_fp32_body.cuh); DRAM traffic is recorded per family."""
     if all(p.radius <= 15 for p in plans) and all((j.W * 4) % 16 == 0 for j in jobs):
         return "fbf_fp32_tma_kernel"
+
+    def tiles(p, j):
+        ty = 128 if p.radius <= 30 else 64
+        return math.ceil(j.W / 32) * math.ceil(j.H / ty)
+    if all(p.radius > 15 and tiles(p, j) >= 3 * sm_count for p, j in zip(plans, jobs)):
+        return "fbf_fp32_carry_kernel"
     return "fbf_fp32_kernel"
 
 
@@ -307,8 +322,9 @@ class _ShardedOracle:
 
 def run_reference(a):
     """Reference arm: the FP64 NumPy oracle as it stands, sharded in row bands across every
-    host core.  Each step filters the first min(H, 64 x cores) rows of each image of the
-    workload (the whole 1024 x 1024 sweep image on 16 cores)."""
+    host core.  Each step filters the first `rows` rows of each image of the workload, with
+    `rows` (a multiple of the core count, at most H) sized from an untimed calibration run so
+    that the whole --warmup + --steps run takes about --ref-seconds."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
@@ -318,9 +334,13 @@ def run_reference(a):
         if j.seed not in imgs:
             imgs[j.seed] = j.image()
     sharded = _ShardedOracle()
-    rows = 64 * sharded.cores
     per = []
     try:
+        cal_rows = 4 * sharded.cores
+        t_cal = sum(sharded.run(imgs[j.seed], j, cal_rows)[1] for j in jobs)
+        per_step = a.ref_seconds / max(1, a.warmup + a.steps)
+        rows = int(per_step / max(t_cal, 1e-6) * cal_rows) // sharded.cores * sharded.cores
+        rows = max(sharded.cores, min(rows, max(j.H for j in jobs)))
         for s in range(a.warmup + a.steps):
             t = 0.0
             px = 0
@@ -336,13 +356,14 @@ def run_reference(a):
     sec = sum(t for _, t in per)
     val = px / sec / 1e6
     sample = (f"per step: the first min(H, {rows}) rows of each image, in row bands with "
-              f"r-row halos on {sharded.cores} spawned processes (wall time)")
+              f"r-row halos on {sharded.cores} spawned processes (wall time; rows sized for "
+              f"about {a.ref_seconds:.0f} s over the run)")
     line = {
         "impl": "reference", "metric": METRIC, "value": val, "unit": "Mpix/s", "n_gpus": a.gpus,
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * sec / len(per),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic",
-        "config": _config(name, jobs, None, "oracle"),
+        "data": "synthetic", "form": "oracle (FP64)",
+        "config": _config(name, jobs),
         "cpu_baseline": {"value": val, "unit": "Mpix/s", "cores": sharded.cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": val, "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -351,15 +372,110 @@ def run_reference(a):
     return 0
 
 
-def _config(name, jobs, plans, form):
-    cfg = {"workload": name, "form": form,
-           "images": [{"H": j.H, "W": j.W, "theta": j.theta, "sigma": j.sigma,
-                       "K_req": j.K, "eps": j.eps} for j in jobs],
-           "l2": "flushed before each timed step (256 MiB write, untimed)"}
-    if plans:
-        for d, p in zip(cfg["images"], plans):
-            d["K"], d["T"], d["E"], d["r"] = p.K, p.T, p.E, p.radius
-    return cfg
+def _config(name, jobs):
+    """The workload: what both arms run (the plans fitted for it are reported beside it)."""
+    return {"workload": name,
+            "images": [{"H": j.H, "W": j.W, "theta": j.theta, "sigma": j.sigma,
+                        "K_req": j.K, "eps": j.eps} for j in jobs]}
+
+
+def _plans_info(plans):
+    return [{"K": p.K, "T": p.T, "E": p.E, "r": p.radius} for p in plans]
+
+
+L2_NOTE = "flushed before each timed step (256 MiB write, untimed)"
+
+
+def _measure_fp32_peak(B, dev, stream, sm_count):
+    """The FP32 multiply-add rate of this GPU, measured with the library's probe
+    (fbf_debug_fp32_peak: 16 independent chains per thread, packed fma.rn.f32x2 pairs and
+    scalar fmaf), timed with CUDA events on the launching stream; best of five launches per
+    variant.  Returns a dict with TFLOP/s per variant and the peak (the larger)."""
+    import torch
+    blocks, threads = 4 * sm_count, 256
+    out = torch.empty(blocks * threads, dtype=torch.float32, device=dev)
+    sh = stream.cuda_stream
+    res = {}
+    for name, pairs in (("ffma2", True), ("ffma", False)):
+        iters = 1 << 17
+        B.fbf_debug_fp32_peak(pairs, blocks, threads, 1 << 10, out.data_ptr(), sh)   # warm-up
+        best = 0.0
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            flop = B.fbf_debug_fp32_peak(pairs, blocks, threads, iters, out.data_ptr(), sh)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            best = max(best, flop / (e0.elapsed_time(e1) / 1e3) / 1e12)
+        res[name] = best
+    res["peak"] = max(res["ffma2"], res["ffma"])
+    res["launch"] = f"{blocks} x {threads} threads, 16 chains x {1 << 17} multiply-adds per thread"
+    return res
+
+
+def _time_steps(B, plans, jobs, x, outs, flush, stream, steps, warmup, world=1):
+    """`warmup` untimed then `steps` timed steps, one step = every job filtered once by
+    fbf_filter; L2 flushed before each step outside the timed region.  Returns the per-step
+    device times and each launch's mean time (ms, CUDA events on the launching stream)."""
+    import torch
+    import torch.distributed as dist
+    sh = stream.cuda_stream
+    dev = x[jobs[0].seed].device
+
+    def step(evs=None):
+        for i, (p, j) in enumerate(zip(plans, jobs)):
+            if evs:
+                evs[i][0].record(stream)
+            B.fbf_filter(p.handle, x[j.seed].data_ptr(), outs[i].data_ptr(), j.H, j.W, j.W, sh)
+            if evs:
+                evs[i][1].record(stream)
+
+    for _ in range(warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    E = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    st_ev = [(E(), E()) for _ in range(steps)]
+    ln_ev = [[(E(), E()) for _ in jobs] for _ in range(steps)]
+    t0 = time.perf_counter()
+    for s in range(steps):
+        flush.zero_()
+        st_ev[s][0].record(stream)
+        step(ln_ev[s])
+        st_ev[s][1].record(stream)
+    torch.cuda.synchronize(dev)
+    wall = time.perf_counter() - t0
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    step_ms = [b.elapsed_time(e) for b, e in st_ev]
+    launch_ms = [statistics.mean(ln_ev[s][i][0].elapsed_time(ln_ev[s][i][1]) for s in range(steps))
+                 for i in range(len(jobs))]
+    return step_ms, launch_ms, wall
+
+
+def _roofline(name, plans, jobs, launch_ms, peak):
+    """FP32 FMA-bound roofline of the fused kernel: algorithmic flops (F(K, r) per pixel)
+    over the summed launch times, against the measured FP32 peak."""
+    flops = [_flops_per_px(p.K, p.radius) * j.H * j.W for p, j in zip(plans, jobs)]
+    achieved = sum(flops) / (sum(launch_ms) / 1e3) / 1e12
+    kern = _fp32_kernel_name(plans, jobs)
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak["peak"], "unit": "TFLOP/s",
+            "frac": achieved / peak["peak"], "traffic": None, "kernel": kern,
+            "peak_source": "measured on this GPU by the FP32 multiply-add probe (fbf_debug_fp32_peak, "
+                           f"{peak['launch']}): {peak['ffma2']:.2f} TFLOP/s packed, {peak['ffma']:.2f} scalar",
+            "frac_of_derived_peak": achieved / peak["derived"], "derived_peak": peak["derived"],
+            "derived_peak_source": peak["derived_source"],
+            "flops_per_px": [_flops_per_px(p.K, p.radius) for p in plans], "launch_ms": launch_ms,
+            "algorithmic_flops_per_step": sum(flops),
+            "algorithmic_bytes_per_step": sum(8 * j.H * j.W for j in jobs)}
+    tr = _traffic_for(kern)
+    if tr and name in tr.get("workloads", {}):
+        roof["traffic"] = tr["workloads"][name]
+    return roof
 
 
 def run_ours(a):
@@ -391,45 +507,16 @@ def run_ours(a):
     stream = torch.cuda.current_stream(dev)
     sh = stream.cuda_stream
     px_step = sum(j.H * j.W for j in jobs)
-    flops = [_flops_per_px(p.K, p.radius) * j.H * j.W for p, j in zip(plans, jobs)]
-
-    def step(evs=None):
-        for i, (p, j) in enumerate(zip(plans, jobs)):
-            if evs:
-                evs[i][0].record(stream)
-            B.fbf_filter(p.handle, x[j.seed].data_ptr(), outs[i].data_ptr(), j.H, j.W, j.W, sh)
-            if evs:
-                evs[i][1].record(stream)
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
 
     clocks = ClockSampler(local)
     if rank == 0:
         clocks.start()
-    for _ in range(a.warmup):
-        flush.zero_()
-        step()
-    torch.cuda.synchronize(dev)
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize(dev)
-    E = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
-    st_ev = [(E(), E()) for _ in range(a.steps)]
-    ln_ev = [[(E(), E()) for _ in jobs] for _ in range(a.steps)]
-    t_wall0 = time.perf_counter()
-    for s in range(a.steps):
-        flush.zero_()
-        st_ev[s][0].record(stream)
-        step(ln_ev[s])
-        st_ev[s][1].record(stream)
-    torch.cuda.synchronize(dev)
-    t_wall = time.perf_counter() - t_wall0
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize(dev)
-    step_ms = [b.elapsed_time(e) for b, e in st_ev]
-    launch_ms = [statistics.mean(ln_ev[s][i][0].elapsed_time(ln_ev[s][i][1]) for s in range(a.steps))
-                 for i in range(len(jobs))]
+    step_ms, launch_ms, t_wall = _time_steps(B, plans, jobs, x, outs, flush, stream, a.steps, a.warmup, world)
     value, total_s = _job_rate(px_step, a.steps, sum(step_ms) / 1e3, world, dev)
     total_ms = 1e3 * total_s
+    peak = _measure_fp32_peak(B, dev, stream, sm_count)
+    peak["derived"], peak["derived_source"] = _fp32_peak_tflops(sm_count)
 
     # ---- end to end through the public API with host buffers --------------------------
     # the C ABI's host-buffer call, on pinned host tensors (pointers resolved once)
@@ -452,33 +539,42 @@ def run_ours(a):
     e2e_val, _ = _job_rate(px_step, e2e_steps, sum(e2e_t), world, dev)
     h2d = sum(4 * j.H * j.W for j in jobs)
     d2h = sum(4 * j.H * j.W for j in jobs)
+    e2e_match = all(torch.equal(host_out[i], outs[i].cpu()) for i in range(len(jobs)))
     clk = clocks.stop() if rank == 0 else None
-
-    # ---- roofline of the fused kernel ---------------------------------------------------
-    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
-    peak, peak_src = _fp32_peak_tflops(sm_count)
-    achieved = sum(flops) / (sum(launch_ms) / 1e3) / 1e12
-    tr = _traffic_for("fbf_fp32_kernel")
-    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": None, "kernel": _fp32_kernel_name(plans, jobs),
-            "peak_source": peak_src + " (derived FP32 FFMA peak)",
-            "flops_per_px": [_flops_per_px(p.K, p.radius) for p in plans],
-            "launch_ms": launch_ms}
-    if tr and name in tr.get("workloads", {}):
-        roof["traffic"] = tr["workloads"][name]
 
     result = {
         "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": _config(name, jobs, plans, "fp32"), "roofline": roof,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "form": "fp32",
+        "config": _config(name, jobs), "plans": _plans_info(plans), "l2": L2_NOTE,
+        "roofline": _roofline(name, plans, jobs, launch_ms, peak),
         "e2e": {"value": e2e_val, "unit": "Mpix/s", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h, "steps": e2e_steps},
+                "d2h_bytes_per_step": d2h, "steps": e2e_steps,
+                "call": "fbf_filter_host (C ABI) on pinned host buffers, wall clock per step",
+                "same_bits_as_device_call": e2e_match},
         "gpu_launches": a.steps * len(jobs), "clocks": clk,
-        "timed_wall_s": t_wall,
+        "timed_wall_s": t_wall, "fp32_peak_probe": peak,
     }
 
-    # ---- CPU baseline: the oracle as it stands, on a bounded sample (rank 0, N = 1) -----
+    # ---- the sigma sweep (1024^2, theta 5), the other single-image workload --------------
+    extra = None
+    if name != "sigma_sweep_1024x1024_theta5" and not a.no_sweep:
+        sname, sjobs = _jobs("sigma_sweep")
+        splans = [B.Plan(j.sigma, 255, j.theta, K=j.K or 0, eps=j.eps or 0.0) for j in sjobs]
+        simg = {j.seed: j.image() for j in sjobs}
+        sx = {s: torch.from_numpy(v).to(dev) for s, v in simg.items()}
+        souts = [torch.empty((j.H, j.W), dtype=torch.float32, device=dev) for j in sjobs]
+        ssteps = max(3, min(a.steps, 100))
+        sms, slaunch, _ = _time_steps(B, splans, sjobs, sx, souts, flush, stream, ssteps, max(3, a.warmup))
+        spx = sum(j.H * j.W for j in sjobs)
+        extra = {"jobs": sjobs, "plans": splans, "imgs": simg, "x": sx, "outs": souts, "launch_ms": slaunch}
+        result["sigma_sweep"] = {
+            "workload": sname, "value": spx * ssteps / (sum(sms) / 1e3) / 1e6, "unit": "Mpix/s",
+            "steps": ssteps, "ms_per_step": sum(sms) / ssteps,
+            "config": _config(sname, sjobs), "plans": _plans_info(splans),
+            "roofline": _roofline(sname, splans, sjobs, slaunch, peak)}
+
+    # ---- CPU baseline and errors: the oracle as it stands (rank 0, N = 1) ----------------
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         one_px = 0
         one_s = 0.0
@@ -486,38 +582,51 @@ def run_ours(a):
             ref, dt = _oracle_band(imgs_np[j.seed], j, a.cpu_rows)
             one_s += dt
             one_px += ref.shape[0] * j.W
-        # every host core, row bands with halos: the whole image when it fits in ~15 s
+        # every host core, row bands with halos: every pixel of every image
         sharded = _ShardedOracle()
         try:
-            budget_px = 15.0 * sharded.cores * one_px / one_s
-            rows = max(sharded.cores, int(budget_px / max(1, px_step / max(1, jobs[0].H))))
             cpu_px = 0
             cpu_s = 0.0
             refs = []
             for j in jobs:
-                ref, dt = sharded.run(imgs_np[j.seed], j, rows)
+                ref, dt = sharded.run(imgs_np[j.seed], j, j.H)
                 refs.append(ref)
                 cpu_s += dt
                 cpu_px += ref.shape[0] * j.W
+            srefs = []
+            if extra:
+                for j in extra["jobs"]:
+                    ref, _ = sharded.run(extra["imgs"][j.seed], j, j.H)
+                    srefs.append(ref)
         finally:
             sharded.close()
-        errs = [float(np.abs(outs[i][: r.shape[0]].cpu().numpy() - r).max())
-                for i, r in enumerate(refs)]
-        covered = [f"{r.shape[0]} of {j.H} rows" for r, j in zip(refs, jobs)]
+        errs = [float(np.abs(outs[i].cpu().numpy() - r).max()) for i, r in enumerate(refs)]
         result["cpu_baseline"] = {
             "value": cpu_px / cpu_s / 1e6, "unit": "Mpix/s", "cores": sharded.cores,
             "kind": "oracle",
-            "sample": f"FP64 NumPy Fourier oracle, row bands with r-row halos on "
-                      f"{sharded.cores} spawned processes (wall time); per image: "
-                      + ", ".join(covered),
+            "sample": f"FP64 NumPy Fourier oracle on every pixel of the step's "
+                      f"{len(jobs)} image(s), row bands with r-row halos on {sharded.cores} "
+                      f"spawned processes (wall time {cpu_s:.1f} s)",
             "single_process": {
                 "value": one_px / one_s / 1e6, "unit": "Mpix/s", "cores": 1,
                 "sample": f"the first {a.cpu_rows} rows (+halo) of each image, one process"}}
         result["error_vs_oracle"] = {"max_abs": max(errs), "per_image": errs, "tolerance": TOL_FP32,
-                                     "sample": "every output pixel the sharded oracle computed: "
-                                               + ", ".join(covered)}
-        result["forms"] = _forms(a, B, jobs, plans, x, launch_ms, refs, flush, stream, dev)
+                                     "meets_tolerance": max(errs) <= TOL_FP32,
+                                     "sample": "every output pixel of every image"}
+        result["forms"] = _forms(a, B, jobs, plans, x, launch_ms, refs, flush, stream, dev, name)
         result["forms"]["fp32"]["max_abs_err"] = max(errs)
+        result["forms"]["fp32"]["meets_tolerance"] = max(errs) <= TOL_FP32
+        if extra:
+            serrs = [float(np.abs(extra["outs"][i].cpu().numpy() - r).max()) for i, r in enumerate(srefs)]
+            sw = result["sigma_sweep"]
+            sw["error_vs_oracle"] = {"max_abs": max(serrs), "per_image": serrs, "tolerance": TOL_FP32,
+                                     "meets_tolerance": max(serrs) <= TOL_FP32,
+                                     "sample": "every output pixel of every image"}
+            sname = sw["workload"]
+            sw["forms"] = _forms(a, B, extra["jobs"], extra["plans"], extra["x"], extra["launch_ms"], srefs,
+                                 flush, stream, dev, sname)
+            sw["forms"]["fp32"]["max_abs_err"] = max(serrs)
+            sw["forms"]["fp32"]["meets_tolerance"] = max(serrs) <= TOL_FP32
     if rank == 0:
         print(json.dumps(result), flush=True)
     if world > 1:
@@ -528,10 +637,12 @@ def run_ours(a):
 TOL_TC = 0.5   # the stated max-abs bound for the 16-bit channel-stack forms (gray levels)
 
 
-def _forms(a, B, jobs, plans, x, fp32_launch_ms, refs, flush, stream, dev):
-    """The precision forms on the same workload: Mpix/s (kernel time, L2 flushed before each
-    step) and max abs error against the same oracle rows as the FP32 line.  The tensor-core
-    forms take r <= 30."""
+def _forms(a, B, jobs, plans, x, fp32_launch_ms, refs, flush, stream, dev, wname):
+    """The precision forms on the same workload: max abs error against the same oracle
+    pixels as the FP32 line, and Mpix/s (kernel time, L2 flushed before each step) only for
+    a form within its stated bound: a rate at a larger error is not comparable (the plain
+    and chosen forms are compared at the same accuracy).  The tensor-core forms take
+    r <= 30."""
     import numpy as np
     import torch
     px = sum(j.H * j.W for j in jobs)
@@ -539,7 +650,7 @@ def _forms(a, B, jobs, plans, x, fp32_launch_ms, refs, flush, stream, dev):
     forms = {"fp32": {"mpix_s": px / (fp32_ms / 1e3) / 1e6, "kernel_ms": fp32_ms,
                       "max_abs_err": None, "tolerance": TOL_FP32}}
     steps = max(3, min(a.steps, 20))
-    for name, prec in (("fp16_tc", B.FBF_FP16_TC), ("bf16_tc", B.FBF_BF16_TC)):
+    for name, prec in (("bf16_tc", B.FBF_BF16_TC), ("fp16_tc", B.FBF_FP16_TC)):
         if any(p.radius > 30 for p in plans):
             forms[name] = {"unavailable": "radius above 30"}
             continue
@@ -561,21 +672,28 @@ def _forms(a, B, jobs, plans, x, fp32_launch_ms, refs, flush, stream, dev):
             e1.record(stream)
         torch.cuda.synchronize(dev)
         ms = statistics.mean(e0.elapsed_time(e1) for e0, e1 in evs)
-        errs = [float(np.abs(y[: r.shape[0]].cpu().numpy() - r).max()) for y, r in zip(ys, refs)]
-        peak = _bf16_peak()
-        alg = sum(_flops_per_px(p.K, p.radius) * j.H * j.W for p, j in zip(tp, jobs)) / (ms / 1e3) / 1e12
-        dense = sum(_tc_mma_flops(p.K, p.radius, j.H, j.W, name == "bf16_tc") for p, j in zip(tp, jobs)) / (ms / 1e3) / 1e12
-        tr = _traffic_for("fbf_tc_kernel")
-        forms[name] = {"mpix_s": px / (ms / 1e3) / 1e6, "kernel_ms": ms, "max_abs_err": max(errs),
-                       "per_image_err": errs, "tolerance": TOL_TC, "meets_tolerance": max(errs) <= TOL_TC,
-                       "speedup_vs_fp32": fp32_ms / ms, "kernel": "fbf_tc_kernel",
-                       "roofline": {"bound": "tensor", "unit": "TFLOP/s", "peak": peak,
-                                    "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst, measured)",
-                                    "achieved_algorithmic": alg, "frac_algorithmic": alg / peak,
-                                    "achieved_dense_mma": dense, "frac_dense_mma": dense / peak,
-                                    "traffic": (tr or {}).get("workloads", {}).get(
-                                        f"{_jobs(a.workload)[0]}/{name}")},
-                       "device_errors": B.fbf_device_errors(True)}
+        errs = [float(np.abs(y.cpu().numpy() - r).max()) for y, r in zip(ys, refs)]
+        ok = max(errs) <= TOL_TC
+        entry = {"max_abs_err": max(errs), "per_image_err": errs, "tolerance": TOL_TC, "meets_tolerance": ok,
+                 "kernel": "fbf_tc_kernel", "device_errors": B.fbf_device_errors(True)}
+        if ok:
+            peak = _bf16_peak()
+            alg = sum(_flops_per_px(p.K, p.radius) * j.H * j.W for p, j in zip(tp, jobs)) / (ms / 1e3) / 1e12
+            dense = sum(_tc_mma_flops(p.K, p.radius, j.H, j.W, name == "bf16_tc")
+                        for p, j in zip(tp, jobs)) / (ms / 1e3) / 1e12
+            tr = _traffic_for("fbf_tc_kernel")
+            entry.update({
+                "mpix_s": px / (ms / 1e3) / 1e6, "kernel_ms": ms, "speedup_vs_fp32": fp32_ms / ms,
+                "roofline": {"bound": "tensor", "unit": "TFLOP/s", "peak": peak,
+                             "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst, measured)",
+                             "achieved_algorithmic": alg, "frac_algorithmic": alg / peak,
+                             "achieved_dense_mma": dense, "frac_dense_mma": dense / peak,
+                             "traffic": (tr or {}).get("workloads", {}).get(f"{wname}/{name}")}})
+        else:
+            entry.update({"mpix_s": None,
+                          "excluded": f"max abs error {max(errs):.3g} above the {TOL_TC} bound: no rate is "
+                                      "quoted for a form outside its stated accuracy"})
+        forms[name] = entry
         for p in tp:
             p.close()
     return forms

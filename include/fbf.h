@@ -149,7 +149,9 @@ int fbf_filter(fbf_plan_t plan, const float* d_in, float* d_out, int H, int W,
  * Arguments, layout and results are those of fbf_filter (FBF_FP32 plans only, else
  * FBF_EUNSUPPORTED).  The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call before any
- * stream capture.  Each call clears the counters it uses on `cuda_stream` before the
+ * stream capture.  The address is kept for the life of the process: after a
+ * cudaDeviceReset no entry point may be called again in that process (this address and the
+ * other calls' cached workspaces would no longer be mapped).  Each call clears the counters it uses on `cuda_stream` before the
  * kernel runs.  All calls share the one array: calls whose work overlaps on the GPU
  * (different streams, or several host threads) race and must be serialised by the caller.
  * Limit: the image may need at most 262144 tiles of 32 columns by 64 to 128 rows
@@ -222,7 +224,11 @@ int fbf_launch(fbf_batch_t batch, void* cuda_stream);
 
 /* fbf_batch_capture -- instead of launching, record the queued images' launch (work-list
  * copy + kernels) as a CUDA graph owned by the batch, replacing any earlier one; the queue
- * is emptied, also when the call fails.  Tuning and allocation happen before the capture. */
+ * is emptied, also when the call fails.  Tuning and allocation happen before the capture.
+ * The graph has its own work-list and split-tile scratch buffers, which later fbf_launch
+ * calls never resize, so launches and replays may be mixed in any order.  A failed capture
+ * that had to grow those buffers leaves no graph (fbf_batch_replay then returns
+ * FBF_EINVAL). */
 int fbf_batch_capture(fbf_batch_t batch, void* cuda_stream);
 
 /* fbf_batch_replay -- launch the captured graph on `cuda_stream` (same pointers and sizes,
@@ -374,6 +380,17 @@ const char* fbf_last_error(void);
  * launches in question.  Clearing a nonzero word also resets the library's cached
  * split-tile counters (synchronising the devices that hold them). */
 int fbf_device_errors(int* flags, int clear);
+
+/* fbf_debug_fp32_peak -- measurement aid, not part of the method: launch a probe of the
+ * FP32 multiply-add rate (blocks x threads threads, each running 16 independent chains of
+ * `iters` packed fma.rn.f32x2 pairs when pairs != 0, else scalar fmaf pairs) on
+ * cuda_stream, and return in *flop the floating-point operations the launch performs
+ * (2 per multiply-add).  Timing the launch with events gives the FP32 peak the fused
+ * filter's roofline is measured against.  d_out: device buffer of blocks x threads floats
+ * (written, to keep the chains live).  threads a multiple of 32 in [32, 256], blocks >= 1,
+ * iters >= 1, else FBF_EINVAL; launch errors FBF_ECUDA. */
+int fbf_debug_fp32_peak(int pairs, int blocks, int threads, long long iters, float* d_out,
+                        void* cuda_stream, double* flop);
 
 /* fbf_version -- library version string. */
 const char* fbf_version(void);

@@ -108,6 +108,8 @@ SIGNATURES = {
     "fbf_device_errors": (ctypes.c_int, [_c_int_p, ctypes.c_int]),
     "fbf_last_error": (ctypes.c_char_p, []),
     "fbf_version": (ctypes.c_char_p, []),
+    "fbf_debug_fp32_peak": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_longlong,
+                                           ctypes.c_void_p, ctypes.c_void_p, _c_double_p]),
     "fbf_debug_error_curve": (ctypes.c_int, [_c_double_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                              _c_double_p]),
 }
@@ -353,6 +355,14 @@ def fbf_last_error() -> str:
 
 def fbf_version() -> str:
     return lib().fbf_version().decode()
+
+
+def fbf_debug_fp32_peak(pairs: bool, blocks: int, threads: int, iters: int, d_out: int, stream) -> float:
+    """Launch the FP32 multiply-add rate probe on `stream`; returns the launch's flop count."""
+    flop = ctypes.c_double(0.0)
+    _check(lib().fbf_debug_fp32_peak(1 if pairs else 0, blocks, threads, iters, ctypes.c_void_p(d_out),
+                                     ctypes.c_void_p(stream), ctypes.byref(flop)), "fbf_debug_fp32_peak")
+    return flop.value
 
 
 def fbf_debug_error_curve(b, R: int, T: int, Kc: int):

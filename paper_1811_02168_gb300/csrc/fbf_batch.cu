@@ -236,8 +236,13 @@ struct Batch {
   ListBuf ring[kRing + 1];               // [kRing] belongs to the graph
   int slot = 0;                          // slot in use by the current prepare/launch
   unsigned long long launches = 0;
-  void* d_scratch = nullptr;
-  size_t counter_cap = 0, partial_cap = 0;
+  // split-tile scratch (tile counters, then partial sums): [0] for fbf_launch, [1] owned by
+  // the captured graph, whose kernels have its addresses baked in
+  struct ScratchBuf {
+    void* d = nullptr;
+    size_t counter_cap = 0, partial_cap = 0;
+  };
+  ScratchBuf scratch[2];
   // graph
   cudaGraphExec_t graph = nullptr;
   cudaStream_t capture_stream = nullptr;
@@ -329,7 +334,19 @@ void layout(ClassPlan& cp, int cand) {
   cp.cand = cand;
 }
 
-int ensure_buffers(Batch* b, size_t list_bytes, size_t counters, size_t partial) {
+// The scratch set of the current prepare: the graph's when capturing (slot kRing).
+Batch::ScratchBuf& cur_scratch(Batch* b) { return b->scratch[b->slot == Batch::kRing ? 1 : 0]; }
+
+// Drop the captured graph before a buffer it reads is freed (a later replay is refused on
+// the host instead of touching freed memory).
+void drop_graph_if_owned(Batch* b) {
+  if (b->slot == Batch::kRing && b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+}
+
+int ensure_buffers(Batch* b, size_t list_bytes, size_t counters, size_t partial, cudaStream_t st) {
   cudaError_t e;
   Batch::ListBuf& lb = b->ring[b->slot];
   if (lb.pending) {   // the copy that last read this slot must have run
@@ -342,6 +359,7 @@ int ensure_buffers(Batch* b, size_t list_bytes, size_t counters, size_t partial)
     if (e != cudaSuccess) return set_error(FBF_ECUDA, std::string("fbf_batch: ") + cudaGetErrorString(e));
   }
   if (lb.cap < list_bytes) {
+    drop_graph_if_owned(b);
     if (lb.h) cudaFreeHost(lb.h);
     if (lb.d) { cudaDeviceSynchronize(); cudaFree(lb.d); }
     lb.h = lb.d = nullptr;
@@ -352,26 +370,35 @@ int ensure_buffers(Batch* b, size_t list_bytes, size_t counters, size_t partial)
     if (e != cudaSuccess) return set_error(FBF_ENOMEM, std::string("fbf_batch: ") + cudaGetErrorString(e));
     lb.cap = list_bytes;
   }
-  if (b->counter_cap < counters || b->partial_cap < partial) {
-    if (b->d_scratch) { cudaDeviceSynchronize(); cudaFree(b->d_scratch); }
-    b->d_scratch = nullptr;
+  Batch::ScratchBuf& sb = cur_scratch(b);
+  if (sb.counter_cap < counters || sb.partial_cap < partial) {
+    drop_graph_if_owned(b);
+    if (sb.d) { cudaDeviceSynchronize(); cudaFree(sb.d); }
+    sb.d = nullptr;
+    sb.counter_cap = sb.partial_cap = 0;
     const size_t cc = std::max(counters + counters / 2, (size_t)1024);
     const size_t pc = partial + partial / 2;
     const size_t cbytes = ((cc * sizeof(int) + 255) / 256) * 256;
-    e = cudaMalloc(&b->d_scratch, cbytes + pc);
-    if (e != cudaSuccess) return set_error(FBF_ENOMEM, std::string("fbf_batch: ") + cudaGetErrorString(e));
-    e = cudaMemset(b->d_scratch, 0, cbytes);   // counters start at zero; launches leave them at zero
+    e = cudaMalloc(&sb.d, cbytes + pc);
+    if (e != cudaSuccess) {
+      sb.d = nullptr;
+      return set_error(FBF_ENOMEM, std::string("fbf_batch: ") + cudaGetErrorString(e));
+    }
+    // counters start at zero (launches leave them at zero), cleared in the order of the
+    // stream that launches next, which may be a non-blocking one
+    e = cudaMemsetAsync(sb.d, 0, cbytes, st);
     if (e != cudaSuccess) return set_error(FBF_ECUDA, std::string("fbf_batch: ") + cudaGetErrorString(e));
-    b->counter_cap = cc;
-    b->partial_cap = pc;
+    sb.counter_cap = cc;
+    sb.partial_cap = pc;
   }
   return FBF_OK;
 }
 
-int* scratch_counters(Batch* b) { return reinterpret_cast<int*>(b->d_scratch); }
+int* scratch_counters(Batch* b) { return reinterpret_cast<int*>(cur_scratch(b).d); }
 float* scratch_partials(Batch* b) {
-  const size_t cbytes = ((b->counter_cap * sizeof(int) + 255) / 256) * 256;
-  return reinterpret_cast<float*>(static_cast<char*>(b->d_scratch) + cbytes);
+  const Batch::ScratchBuf& sb = cur_scratch(b);
+  const size_t cbytes = ((sb.counter_cap * sizeof(int) + 255) / 256) * 256;
+  return reinterpret_cast<float*>(static_cast<char*>(sb.d) + cbytes);
 }
 
 void write_lists(Batch* b, const std::vector<ClassPlan>& cps) {
@@ -432,7 +459,7 @@ int prepare(Batch* b, std::vector<ClassPlan>* cps, size_t* list_bytes, cudaStrea
           size_t pb = 0;
           rc = cands[j].partial_bytes(b->dev, &pb);
           if (rc != FBF_OK) return rc;
-          rc = ensure_buffers(b, *list_bytes, (size_t)one.tiles, pb);
+          rc = ensure_buffers(b, *list_bytes, (size_t)one.tiles, pb, st);
           if (rc != FBF_OK) return rc;
           std::vector<ClassPlan> v{one};
           write_lists(b, v);
@@ -471,7 +498,7 @@ int prepare(Batch* b, std::vector<ClassPlan>* cps, size_t* list_bytes, cudaStrea
     counters = std::max(counters, (size_t)cp.tiles);
     partial = std::max(partial, pb);
   }
-  rc = ensure_buffers(b, *list_bytes, counters, partial);
+  rc = ensure_buffers(b, *list_bytes, counters, partial, st);
   if (rc != FBF_OK) return rc;
   write_lists(b, *cps);
   return FBF_OK;
@@ -549,13 +576,14 @@ int fbf_batch_create(fbf_batch_t* out, int max_images, int flags) try {
 } FBF_ABI_CATCH("fbf_batch_create")
 
 int fbf_submit(fbf_batch_t batch, fbf_plan_t plan, const float* d_in, float* d_out, int H, int W,
-               size_t pitch_elems, fbf_ticket_t* ticket) try {
+                     size_t pitch_elems, fbf_ticket_t* ticket) try {
   if (!batch || !plan) return fbf::set_error(FBF_EINVAL, "fbf_submit: NULL batch or plan");
   if (!d_in || !d_out) return fbf::set_error(FBF_EINVAL, "fbf_submit: NULL image pointer");
   if (H < 1 || W < 1) return fbf::set_error(FBF_EINVAL, "fbf_submit: H and W must be >= 1");
   if (pitch_elems < (size_t)W) return fbf::set_error(FBF_EINVAL, "fbf_submit: pitch < W");
   const fbf::Plan* p = fbf::plan_of(plan);
-  if (fbf::class_of(p->r, p->precision) < 0) return fbf::set_error(FBF_EUNSUPPORTED, "fbf_submit: radius too large for the plan's form");
+  if (fbf::class_of(p->r, p->precision) < 0)
+    return fbf::set_error(FBF_EUNSUPPORTED, "fbf_submit: radius too large for the plan's form");
   const size_t span = ((size_t)(H - 1) * pitch_elems + (size_t)W) * sizeof(float);
   const char* a = (const char*)d_in;
   const char* o = (const char*)d_out;
@@ -704,7 +732,8 @@ int fbf_batch_destroy(fbf_batch_t batch) try {
     if (lb.d) cudaFree(lb.d);
     if (lb.h) cudaFreeHost(lb.h);
   }
-  if (b.d_scratch) cudaFree(b.d_scratch);
+  for (auto& sb : b.scratch)
+    if (sb.d) cudaFree(sb.d);
   delete batch;
   return FBF_OK;
 } FBF_ABI_CATCH("fbf_batch_destroy")

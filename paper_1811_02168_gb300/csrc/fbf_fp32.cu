@@ -175,10 +175,13 @@ bool encode_f_map(CUtensorMap* map, const float* in, int H, int W, size_t pitch,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NAN_REQUEST_ZERO_FMA) == CUDA_SUCCESS;
 }
 
-// SMs and resident CTAs of one instantiation on one device (set once per device)
+// SMs and resident CTAs of one instantiation on one device (set once per device, under a
+// lock: several host threads may launch at once)
+std::mutex g_slots_mu;
 template <class KernelFn>
 int kernel_slots(KernelFn fn, int nt, size_t smem, int dev, int* sms_out, int* occ_out,
                  int* cache_sms, int* cache_occ, const char* who) {
+  std::lock_guard<std::mutex> lk(g_slots_mu);
   if (!cache_occ[dev]) {
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return set_error(FBF_ECUDA, std::string(who) + ": " + cudaGetErrorString(e));
@@ -194,6 +197,9 @@ int kernel_slots(KernelFn fn, int nt, size_t smem, int dev, int* sms_out, int* o
   *occ_out = cache_occ[dev];
   return FBF_OK;
 }
+
+// Carried rows are used when the image has at least this many tiles per CTA.
+constexpr long long kCarryMinTilesPerCta = 3;
 
 Work single_work(const float* in, float* out, int H, int W, size_t pitch, int K, int TY, int row0 = 0,
                  int rows = 0) {
@@ -250,13 +256,38 @@ int launch_cfg(const DeviceParams& dp, const float* in, float* out, int H, int W
   sc.wtot = w.tiles * w.wtile;
   long long G = (long long)nsm * nocc;
   if (G > sc.wtot) G = sc.wtot;
+  // Carried x-pass rows pay when each CTA's range covers several tiles of a strip (the
+  // first tile of a range convolves all its rows); radii <= 15 gain no whole x-pass round.
+  constexpr int CSLOT = 2 * carry_rows(RAD, 4) * TX;
+  constexpr bool kCarryCfg = RAD > 15;
+  const bool carry = kCarryCfg && !tma && w.tiles >= kCarryMinTilesPerCta * G;
+  if constexpr (kCarryCfg) {
+    if (carry) {
+      static int occ_c[64] = {0};
+      static int sms_c[64] = {0};
+      int nsm_c = 0, nocc_c = 0;
+      rc = kernel_slots(fbf_fp32_carry_kernel<RAD, TY, NT, NY>, NT, C::SMEM_BYTES, dev, &nsm_c, &nocc_c,
+                        sms_c, occ_c, "fbf_filter");
+      if (rc != FBF_OK) return rc;
+      if ((long long)nsm_c * nocc_c != G)
+        return set_error(FBF_ECUDA, "fbf_filter: carried-row kernel occupancy differs");
+    }
+  }
   const size_t partial_bytes = (size_t)G * 2 * 2 * NY * NT * sizeof(float);
-  rc = get_workspace(dev, st, partial_bytes, (size_t)w.tiles, &sc.partial, &sc.counter);
+  const size_t carry_bytes = carry ? (size_t)G * dp.K * CSLOT * sizeof(float2) : 0;
+  rc = get_workspace(dev, st, align256(partial_bytes) + carry_bytes, (size_t)w.tiles, &sc.partial, &sc.counter);
   if (rc != FBF_OK) return rc;
+  if (carry) sc.carry = reinterpret_cast<float2*>(reinterpret_cast<char*>(sc.partial) + align256(partial_bytes));
   bool launched = false;
   if constexpr (C::TMA_OK) {
     if (tma) {
       fbf_fp32_tma_kernel<RAD, TY, NT, NY><<<(unsigned)G, NT, C::TMA_SMEM_BYTES, st>>>(p, w, sc, map);
+      launched = true;
+    }
+  }
+  if constexpr (kCarryCfg) {
+    if (!launched && carry) {
+      fbf_fp32_carry_kernel<RAD, TY, NT, NY><<<(unsigned)G, NT, C::SMEM_BYTES, st>>>(p, w, sc);
       launched = true;
     }
   }

@@ -48,6 +48,10 @@ __device__ __forceinline__ void tma_load_box(float* dst, const CUtensorMap* map,
                " [%0], [%1, {%2, %3}], [%4];"
                :: "r"(smem_addr(dst)), "l"(map), "r"(x), "r"(y), "r"(smem_addr(bar)) : "memory");
 }
+// 16-byte asynchronous copy global -> shared (completed by cp.async.wait_all)
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" :: "r"(smem_addr(smem_dst)), "l"(gsrc) : "memory");
+}
 __device__ __forceinline__ bool tma_bar_wait(unsigned long long* bar, uint32_t parity) {
   const uint32_t a = smem_addr(bar);
   unsigned long long t0 = 0;
@@ -135,11 +139,13 @@ struct Scratch {
   long long wtot;                     // total weight of the launch
   float* partial;                     // G * 2 slots * 2 * NY * NT floats
   int* counter;                       // one per tile of every image, zero between launches
+  float2* carry;                      // carried x-pass rows (SingleSrcCarry): G * K slots
 };
 
 // A single image whose parameters sit in the constant bank (kernel parameter).
 struct SingleSrc {
   static constexpr bool kTma = false;
+  static constexpr bool kCarry = false;
   const DeviceParams* p;
   Work w;
   __device__ __forceinline__ int count() const { return 1; }
@@ -153,6 +159,7 @@ struct SingleSrc {
 // elements outside the image).
 struct SingleSrcTma {
   static constexpr bool kTma = true;
+  static constexpr bool kCarry = false;
   const DeviceParams* p;
   Work w;
   const CUtensorMap* map;
@@ -162,9 +169,33 @@ struct SingleSrcTma {
   __device__ __forceinline__ int find(long long) const { return 0; }
 };
 
+// A single image filtered strip by strip with the x-pass halo carried down each strip.
+// Tiles are numbered column-major (tile t is row t % tiles_y of strip t / tiles_y), so the
+// tiles of a CTA's range walk down a strip.  The y pass of a tile needs the x-pass rows
+// [0, 2r) of its buffer, which are rows [TY, TY + 2r) of the tile above: when the CTA
+// filtered term k of the tile above, it left those rows in its carry slot (sc.carry) and the
+// tile reloads them instead of convolving them again, so the x pass covers TY new rows per
+// tile instead of TY + 2r.  A tile at the top of a strip or at the start of the CTA's range
+// (or a term the CTA did not filter for the tile above) convolves all its rows.
+struct SingleSrcCarry {
+  static constexpr bool kTma = false;
+  static constexpr bool kCarry = true;
+  const DeviceParams* p;
+  Work w;
+  __device__ __forceinline__ int count() const { return 1; }
+  __device__ __forceinline__ Work work(int) const { return w; }
+  __device__ __forceinline__ const DeviceParams& params(int) const { return *p; }
+  __device__ __forceinline__ int find(long long) const { return 0; }
+};
+
+// rows of the x-pass buffer a tile can take over from the tile above: the largest multiple
+// of the row-group height (4 rows for k >= 1, 8 for k = 0) not above 2r
+__host__ __device__ constexpr int carry_rows(int rad, int group) { return (2 * rad) / group * group; }
+
 // A device work-list of images (batched launch).
 struct ListSrc {
   static constexpr bool kTma = false;
+  static constexpr bool kCarry = false;
   const DeviceParams* __restrict__ prm;
   const Work* __restrict__ wl;
   int n;
@@ -298,6 +329,14 @@ __device__ __forceinline__ void fbf_body(const Src& src, const Scratch& sc) {
   using C = Cfg<RAD, TY, NT, NY>;
   constexpr bool TMA = Src::kTma;
   static_assert(!TMA || C::TMA_OK, "TMA staging does not fit this configuration");
+  // carried x-pass rows (SingleSrcCarry): rows [0, CS) of a term's buffer come from the tile
+  // above, rows [CS, XR) are convolved; CSLOT float2 per (CTA, term) slot
+  constexpr bool CARRY = Src::kCarry;
+  static_assert(!(TMA && CARRY), "carried tiles take the plain f staging");
+  constexpr int CS1 = carry_rows(RAD, 4), CS0 = carry_rows(RAD, 8);
+  constexpr int XR4 = (C::HROWS + 3) / 4 * 4, XR8 = (C::HROWS + 7) / 8 * 8;
+  constexpr int CSLOT = 2 * CS1 * TX;
+  static_assert(XR8 <= C::HROWS_P && TY + CS1 <= C::HROWS, "carried rows must lie inside the buffer");
   constexpr int FS = TMA ? C::TMA_BW : C::FHS;        // f-halo row stride (floats)
   extern __shared__ float4 smem_f4[];
   // TMA: two f buffers first (128-byte aligned), then the plain path's layout without its f.
@@ -368,8 +407,10 @@ __device__ __forceinline__ void fbf_body(const Src& src, const Scratch& sc) {
     const long long t = u / K;
     const int kb = (int)(u - t * K);
     const int ke = (img == img_end && t == u_end / K) ? (int)(u_end - t * K) : K;
-    const int tx0 = (int)(t % wk.tiles_x) * TX;
-    const int ty0 = wk.row0 + (int)(t / wk.tiles_x) * TY;
+    // tile coordinates: row-major, or column-major (strips) when rows are carried
+    const int tyi = CARRY ? (int)(t % wk.tiles_y) : (int)(t / wk.tiles_x);
+    const int tx0 = (int)(CARRY ? t / wk.tiles_y : t % wk.tiles_x) * TX;
+    const int ty0 = wk.row0 + tyi * TY;
 
     // f of the tile plus halo (rows padded to whole x-pass rounds); kOutside marks
     // pixels outside the image.  The tile uses the term tables when all its values are
@@ -461,9 +502,24 @@ __device__ __forceinline__ void fbf_body(const Src& src, const Scratch& sc) {
 
     for (int k = kb; k < ke; ++k) {
       const float kf = (float)k;
+      // carried rows: this CTA filtered term k of the tile above, whose buffer rows
+      // [TY, TY + cs) are this tile's rows [0, cs); they are copied in while the new rows
+      // are generated and convolved
+      const int cs = (k == 0) ? CS0 : CS1;
+      const int ncs = ((k == 0) ? 1 : 2) * cs * (TX / 2);   // 16-byte chunks
+      const bool carried = CARRY && tyi > 0 && (t - 1) * K + k >= u_first;
+      float2* const slot = CARRY ? sc.carry + ((long long)c * K + k) * CSLOT : nullptr;
+      if (CARRY && carried) {
+        for (int i = tid; i < ncs; i += NT) {
+          const int cp = i / (cs * (TX / 2)), rem = i - cp * cs * (TX / 2);
+          const int row = rem / (TX / 2), col = (rem - row * (TX / 2)) * 2;
+          cp_async16(hbuf + cp * C::CPS + row * C::HS2 + col, slot + (cp * CS1 + row) * TX + col);
+        }
+      }
+      const int xr0 = carried ? cs : 0;
       if (k == 0) {
         // ---- term 0: pair (f - m, 1); eight halo rows per warp iteration -------------
-        for (int rb = warp * 8; rb < C::HROWS_P; rb += C::NW * 8) {
+        for (int rb = xr0 + warp * 8; rb < (carried ? XR8 : C::HROWS_P); rb += C::NW * 8) {
 #pragma unroll
           for (int r8 = 0; r8 < 8; ++r8) {
 #pragma unroll
@@ -480,7 +536,7 @@ __device__ __forceinline__ void fbf_body(const Src& src, const Scratch& sc) {
       } else {
         // ---- term k >= 1: pairs (C, S) and (f'C, f'S); four halo rows per iteration --
         const float2* tab = tabs + (k & 1) * TABN;
-        for (int rb = warp * 4; rb < C::HROWS_P; rb += C::NW * 4) {
+        for (int rb = xr0 + warp * 4; rb < (carried ? XR4 : C::HROWS_P); rb += C::NW * 4) {
           if (tile_int && interior) {
 #pragma unroll
             for (int r4 = 0; r4 < 4; ++r4) {
@@ -530,7 +586,19 @@ __device__ __forceinline__ void fbf_body(const Src& src, const Scratch& sc) {
           __syncwarp();
         }
       }
+      if (CARRY && carried) asm volatile("cp.async.wait_all;" ::: "memory");
       __syncthreads();
+      // rows [TY, TY + cs) are rows [0, cs) of the next tile of the strip: keep them for it
+      // when this CTA filters its term k (same chunk per thread as the load above, so each
+      // thread rereads only what it wrote itself)
+      if (CARRY && tyi + 1 < wk.tiles_y && (img < img_end || (t + 1) * K + k < u_end)) {
+        for (int i = tid; i < ncs; i += NT) {
+          const int cp = i / (cs * (TX / 2)), rem = i - cp * cs * (TX / 2);
+          const int row = rem / (TX / 2), col = (rem - row * (TX / 2)) * 2;
+          *reinterpret_cast<float4*>(slot + (cp * CS1 + row) * TX + col) =
+              *reinterpret_cast<const float4*>(hbuf + cp * C::CPS + (TY + row) * C::HS2 + col);
+        }
+      }
       // the next term's table goes to the other buffer while this term's is still read
       if (tile_int && k + 1 < ke) build_term_table<NT>(p, k + 1, tabs + ((k + 1) & 1) * TABN);
 
@@ -660,6 +728,14 @@ __global__ void __launch_bounds__(NT, 1)
 fbf_fp32_tma_kernel(const __grid_constant__ DeviceParams p, const Work w, const Scratch sc,
                     const __grid_constant__ CUtensorMap map) {
   const SingleSrcTma src{&p, w, &map};
+  fbf_body<RAD, TY, NT, NY>(src, sc);
+}
+
+// One image, parameters in the constant bank, x-pass halo rows carried down each strip.
+template <int RAD, int TY, int NT, int NY>
+__global__ void __launch_bounds__(NT, 1)
+fbf_fp32_carry_kernel(const __grid_constant__ DeviceParams p, const Work w, const Scratch sc) {
+  const SingleSrcCarry src{&p, w};
   fbf_body<RAD, TY, NT, NY>(src, sc);
 }
 

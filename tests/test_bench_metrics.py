@@ -49,8 +49,12 @@ def test_dense_tensor_work_counts_padding_and_compensation():
 def test_fp32_instantiation_name():
     plan15 = SimpleNamespace(radius=15)
     plan30 = SimpleNamespace(radius=30)
-    job = SimpleNamespace(W=1024)
-    odd = SimpleNamespace(W=1023)
+    job = SimpleNamespace(W=1024, H=1024)
+    odd = SimpleNamespace(W=1023, H=1024)
     assert bench._fp32_kernel_name([plan15], [job]) == "fbf_fp32_tma_kernel"
     assert bench._fp32_kernel_name([plan30], [job]) == "fbf_fp32_kernel"
     assert bench._fp32_kernel_name([plan15], [odd]) == "fbf_fp32_kernel"
+    # r > 15 with at least three 32 x 128 tiles per SM: rows carried down the strips
+    big = SimpleNamespace(W=4096, H=4096)
+    assert bench._fp32_kernel_name([plan30], [big]) == "fbf_fp32_carry_kernel"
+    assert bench._fp32_kernel_name([plan30], [big], sm_count=2000) == "fbf_fp32_kernel"

@@ -16,7 +16,7 @@ def _run(extra_env):
     env = {k: v for k, v in os.environ.items() if k not in ("RANK", "WORLD_SIZE", "LOCAL_RANK")}
     env.update(extra_env)
     return subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
-                           "--steps", "1", "--warmup", "3"], cwd=ROOT, env=env, capture_output=True,
+                           "--steps", "1", "--warmup", "3", "--ref-seconds", "4"], cwd=ROOT, env=env, capture_output=True,
                           text=True, timeout=600)
 
 
@@ -29,7 +29,9 @@ def test_reference_arm_line():
     assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == "Mpix/s"
     assert d["higher_is_better"] is True and d["steps"] == 1 and d["warmup"] == 3 and d["n_gpus"] == 1
     assert d["value"] > 0 and d["ms_per_step"] > 0
-    assert d["config"]["workload"] == "sigma_sweep_1024x1024_theta5"
+    assert d["config"]["workload"] == "large_4096x4096_theta10_sigma10_K16"
+    # the same workload description as the GPU arm's line (the plans are reported beside it)
+    assert d["config"] == bench._config(*bench._jobs("large"))
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     e2e = d["e2e"]

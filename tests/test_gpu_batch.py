@@ -124,6 +124,60 @@ def test_graph_capture_and_replay_follow_new_input(B):
     batch.close()
 
 
+def test_replay_after_a_larger_launch(B):
+    """Capture a small batch, then launch a larger one through fbf_launch (its scratch must
+    grow), then replay the graph: the graph keeps its own buffers, so the replay still
+    equals fbf_filter image by image, and one image matches the oracle."""
+    small = _mixed_jobs(3, 21)
+    batch = B.Batch(16)
+    items = []
+    for H, W, theta, sigma, K, seed in small:
+        plan = B.Plan(sigma, 255, theta, K=K)
+        x = torch.from_numpy(voronoi_image(H, W, 8, 30.0, 10.0, seed=seed)).cuda()
+        y = torch.empty_like(x)
+        batch.submit(plan, x, y)
+        items.append((plan, x, y))
+    batch.capture()
+    big_plan = B.Plan(30.0, 255, 5.0, K=6)
+    bigs = [torch.from_numpy(voronoi_image(1500, 1400, 60, 30.0, 10.0, seed=500 + i)).cuda() for i in range(3)]
+    outs = [torch.empty_like(x) for x in bigs]
+    for x, y in zip(bigs, outs):
+        batch.submit(big_plan, x, y)
+    batch.launch()
+    t = batch.replay()
+    batch.wait(t, 60.0)
+    for plan, x, y in items:
+        assert _close(y, _single(B, plan, x))
+    for x, y in zip(bigs, outs):
+        assert _close(y, _single(B, big_plan, x))
+    plan, x, y = items[0]
+    op = ofit.make_plan(plan.sigma, 255, K=plan.K)
+    ref = ofl.fourier_bf(x.cpu().numpy().astype(np.float64), plan.theta, op.c, op.T)
+    assert np.abs(y.cpu().numpy() - ref).max() <= TOL
+    batch.close()
+
+
+def test_first_launch_on_a_non_blocking_stream(B):
+    """The first launch of a fresh batch (its scratch just allocated and cleared) on a
+    non-blocking stream, which is not ordered after the legacy default stream: the result
+    equals fbf_filter."""
+    plan = B.Plan(10.0, 255, 5.0, eps=0.01)
+    xs = [torch.from_numpy(voronoi_image(700 + 13 * i, 650, 40, 30.0, 10.0, seed=40 + i)).cuda() for i in range(4)]
+    ys = [torch.full_like(x, -1.0) for x in xs]
+    refs = [_single(B, plan, x) for x in xs]
+    torch.cuda.synchronize()
+    side = torch.cuda.Stream()
+    batch = B.Batch(8)
+    t = 0
+    for x, y in zip(xs, ys):
+        t = batch.submit(plan, x, y)
+    batch.launch(side)
+    batch.wait(t, 60.0)
+    for y, r in zip(ys, refs):
+        assert _close(y, r)
+    batch.close()
+
+
 def test_launches_in_a_row_reuse_the_work_list_ring(B):
     """More launches than work-list slots, without synchronising in between."""
     plan = B.Plan(30.0, 255, 2.0, K=4)

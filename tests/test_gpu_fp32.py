@@ -225,3 +225,38 @@ def test_ten_bit_image(B):
     assert (plan.K, plan.T) == (op.K, op.T)
     ref = ofl.fourier_bf(img.astype(np.float64), 2.0, op.c, op.T)
     assert np.abs(_gpu(B, plan, img) - ref).max() <= 4 * TOL   # scale: 4x the 8-bit range
+
+
+@pytest.mark.parametrize("H,W,theta,K", [(2050, 1000, 10.0, 4), (2100, 760, 8.0, 5), (1640, 600, 16.0, 3)])
+def test_carried_rows_whole_image(B, H, W, theta, K):
+    """Images with at least three tiles per SM at r > 15 take the kernel that carries the
+    x-pass halo rows down each strip (r = 30, 24 and 48 instantiations; ragged in x and y):
+    every pixel against the FP64 oracle, and against the allocation-free entry point, which
+    always convolves every halo row (the two differ only in where the split tiles' partial
+    sums are cut)."""
+    img = voronoi_image(H, W, 120, 40.0, 12.0, seed=H + W)
+    plan = B.Plan(30.0, 255, theta, K=K)
+    op = _oracle_plan(30.0, K=K)
+    assert (plan.K, plan.T) == (op.K, op.T)
+    ref = ofl.fourier_bf(img.astype(np.float64), theta, op.c, op.T)
+    out = _gpu(B, plan, img)
+    assert np.abs(out - ref).max() <= TOL
+    x = torch.from_numpy(img).cuda()
+    y = torch.full_like(x, -7.0)
+    st = torch.cuda.current_stream()
+    B.fbf_filter_noalloc(plan.handle, x.data_ptr(), y.data_ptr(), H, W, W, st.cuda_stream)
+    st.synchronize()
+    assert np.abs(y.cpu().numpy() - out).max() <= 1e-3
+
+
+def test_carried_rows_mixed_phase_paths(B):
+    """Carried rows cross from tiles with non-integer values (general phase path) into
+    8-bit tiles (term tables) and back: every pixel against the oracle."""
+    H, W = 2048, 1024
+    img = voronoi_image(H, W, 100, 40.0, 10.0, seed=77)
+    rng = np.random.default_rng(78)
+    img[700:900] = (img[700:900] * 0.9 + rng.uniform(0.0, 0.999, (200, W))).astype(np.float32)
+    plan = B.Plan(20.0, 255, 10.0, K=4)
+    op = _oracle_plan(20.0, K=4)
+    ref = ofl.fourier_bf(img.astype(np.float64), 10.0, op.c, op.T)
+    assert np.abs(_gpu(B, plan, img) - ref).max() <= TOL

@@ -63,3 +63,30 @@ def test_noalloc_rejects_images_beyond_its_scratch(B):
         B.fbf_filter_noalloc(plan.handle, 1 << 36, 1 << 40, H, W, W, 0)
     assert ei.value.code == B.FBF_EUNSUPPORTED
     assert "tiles" in B.fbf_last_error()
+
+
+def test_noalloc_allocates_no_device_memory(B):
+    """After one warm-up call, a call on a stream not used before, with an image size not
+    seen before, leaves the device's free memory unchanged: no workspace is created for the
+    new stream and nothing is allocated (buffers and stream are made before the reading)."""
+    plan = B.Plan(10.0, 255, 10.0, K=16)
+    img = voronoi_image(256, 200, 10, 40.0, 10.0, seed=1)
+    x = torch.from_numpy(img).cuda()
+    y = torch.empty_like(x)
+    st = torch.cuda.current_stream()
+    B.fbf_filter_noalloc(plan.handle, x.data_ptr(), y.data_ptr(), 256, 200, 200, st.cuda_stream)
+    st.synchronize()
+    img2 = voronoi_image(900, 700, 30, 40.0, 10.0, seed=2)
+    x2 = torch.from_numpy(img2).cuda()
+    y2 = torch.full_like(x2, -1.0)
+    ref = torch.full_like(x2, -1.0)
+    side = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    B.fbf_filter_noalloc(plan.handle, x2.data_ptr(), y2.data_ptr(), 900, 700, 700, side.cuda_stream)
+    side.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0, free1)
+    B.fbf_filter(plan.handle, x2.data_ptr(), ref.data_ptr(), 900, 700, 700, st.cuda_stream)
+    st.synchronize()
+    assert float((y2 - ref).abs().max()) <= TOL
