@@ -63,6 +63,14 @@ extern "C" {
                               8-bit images, 0.08 at small denominators, against 0.003
                               for FBF_FP32)                                             */
 
+/* Names of the precision forms in the problem statement's terms: the BF16 channel stack with
+   FP32 accumulation is the compensated form, whose y pass is a TF32 banded-Toeplitz
+   contraction on the tensor cores.  (A TF32-operand x pass would carry FP16's 10-bit
+   mantissa, the precision that misses the 0.5 bound at small denominators, so no separate
+   form is built for it.) */
+#define FBF_BF16       FBF_BF16_TC
+#define FBF_TF32_TC    FBF_BF16_TC
+
 /* ---- flags (fbf_plan's `flags`) ----------------------------------------------- */
 #define FBF_FLAG_FIXED_PERIOD 1  /* T = R (fixed period, the FBF model the paper
                                     compares against, Section III); least squares only */
@@ -190,7 +198,7 @@ typedef uint64_t fbf_ticket_t;
 #define FBF_BATCH_AUTOTUNE 1   /* time each candidate tile configuration on first use */
 
 /*
- * fbf_batch_create -- a batch context.  Images are queued with fbf_submit and filtered
+ * fbf_batch_create -- a batch context.  Images are queued with fbf_batch_submit and filtered
  * together by fbf_launch: per precision form and radius class (the kernel instantiation
  * serving their r = ceil(3 theta)) one persistent stream-K launch runs over a device
  * work-list of all
@@ -207,15 +215,15 @@ typedef uint64_t fbf_ticket_t;
 int fbf_batch_create(fbf_batch_t* out, int max_images, int flags);
 
 /*
- * fbf_submit -- queue one image (host-side only; nothing runs until fbf_launch).  Arguments
- * as fbf_filter, any precision form.  The plan must stay alive until the fbf_launch or
- * fbf_batch_capture call that takes the image returns (its parameters are copied then).
- * *ticket (may be NULL) identifies the launch the image will belong to.
+ * fbf_batch_submit -- queue one image (host-side only; nothing runs until fbf_launch).
+ * Arguments as fbf_filter, any precision form.  The plan's parameters are copied, so the
+ * plan may be destroyed right after the call.  *ticket (may be NULL) identifies the launch
+ * the image will belong to.
  * Errors: FBF_EINVAL (bad arguments), FBF_EBUSY (max_images already queued),
  * FBF_EUNSUPPORTED (radius beyond the form's limit: FBF_MAX_RADIUS, FBF_MAX_RADIUS_TC).
  */
-int fbf_submit(fbf_batch_t batch, fbf_plan_t plan, const float* d_in, float* d_out, int H, int W,
-               size_t pitch_elems, fbf_ticket_t* ticket);
+int fbf_batch_submit(fbf_batch_t batch, fbf_plan_t plan, const float* d_in, float* d_out, int H, int W,
+                     size_t pitch_elems, fbf_ticket_t* ticket);
 
 /* fbf_launch -- upload the work-list of the queued images and launch them on `cuda_stream`
  * (asynchronous); the queue is emptied, also when the call fails (the queued images'
@@ -235,14 +243,40 @@ int fbf_batch_capture(fbf_batch_t batch, void* cuda_stream);
  * current image contents); *ticket (may be NULL) names this replay. */
 int fbf_batch_replay(fbf_batch_t batch, void* cuda_stream, fbf_ticket_t* ticket);
 
-/* fbf_poll -- non-blocking: *status = FBF_DONE when the ticket's launch has completed on
- * the device, FBF_PENDING while it runs or is not launched yet.  A device error of the
+/* fbf_batch_poll -- non-blocking: *status = FBF_DONE when the ticket's launch has completed
+ * on the device, FBF_PENDING while it runs or is not launched yet.  A device error of the
  * launch is returned as FBF_ECUDA. */
-int fbf_poll(fbf_batch_t batch, fbf_ticket_t ticket, int* status);
+int fbf_batch_poll(fbf_batch_t batch, fbf_ticket_t ticket, int* status);
 
-/* fbf_wait -- block until the ticket's launch completes or timeout_s seconds pass
+/* fbf_batch_wait -- block until the ticket's launch completes or timeout_s seconds pass
  * (FBF_ETIMEDOUT; a ticket whose launch never happens times out). */
-int fbf_wait(fbf_batch_t batch, fbf_ticket_t ticket, double timeout_s);
+int fbf_batch_wait(fbf_batch_t batch, fbf_ticket_t ticket, double timeout_s);
+
+/*
+ * fbf_submit -- queue one image on the calling thread's current device without a batch
+ * handle: each device has one implicit queue and one library stream (non-blocking, created
+ * on first use, kept until the process exits).  Arguments as fbf_filter (device pointers,
+ * any precision form; the plan's parameters are copied, so the plan may be destroyed after
+ * the call).  The queue is launched -- all its images in one batched launch, as fbf_launch --
+ * at the first fbf_poll or fbf_wait of one of its tickets, or when it already holds 4096
+ * images.  The library stream is not ordered after the caller's streams: d_in must hold the
+ * image (its producer synchronised) when fbf_submit is called, and d_out holds the result
+ * once fbf_poll has reported FBF_DONE.  The caller keeps both alive until then.
+ * *ticket (may be NULL) names the image's launch.  Errors: as fbf_batch_submit, FBF_ECUDA
+ * when the device's queue cannot be set up.
+ */
+int fbf_submit(fbf_plan_t plan, const float* d_in, float* d_out, int H, int W, size_t pitch_elems,
+               fbf_ticket_t* ticket);
+
+/* fbf_poll -- non-blocking state of a ticket from fbf_submit: launches the ticket's queue if
+ * it has not been launched yet, then *status = FBF_DONE when the launch has completed on the
+ * device, FBF_PENDING otherwise.  FBF_EINVAL for a ticket no fbf_submit returned (its
+ * device has no queue); a device error of the launch is returned as FBF_ECUDA. */
+int fbf_poll(fbf_ticket_t ticket, int* status);
+
+/* fbf_wait -- as fbf_poll, then block until the launch completes or timeout_s seconds
+ * pass (FBF_ETIMEDOUT). */
+int fbf_wait(fbf_ticket_t ticket, double timeout_s);
 
 /* fbf_batch_pending -- number of queued, not yet launched images. */
 int fbf_batch_pending(fbf_batch_t batch, int* n);

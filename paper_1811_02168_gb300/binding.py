@@ -20,6 +20,7 @@ FBF_PENDING, FBF_DONE, FBF_EUNSUPPORTED = 6, 7, 8
 FBF_FP32 = 0
 FBF_FP16_TC = 1
 FBF_BF16_TC = 2
+FBF_BF16 = FBF_TF32_TC = FBF_BF16_TC   # the problem statement's names for the compensated form
 FBF_FLAG_FIXED_PERIOD = 1
 FBF_MAX_K = 64
 FBF_MAX_RADIUS = 48
@@ -80,14 +81,18 @@ SIGNATURES = {
     "fbf_lut_load": (ctypes.c_int, [_c_void_pp, ctypes.c_char_p]),
     "fbf_lut_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "fbf_batch_create": (ctypes.c_int, [_c_void_pp, ctypes.c_int, ctypes.c_int]),
-    "fbf_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
-                                  ctypes.c_int, ctypes.c_int, ctypes.c_size_t,
-                                  ctypes.POINTER(ctypes.c_uint64)]),
+    "fbf_batch_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_int, ctypes.c_int, ctypes.c_size_t,
+                                        ctypes.POINTER(ctypes.c_uint64)]),
+    "fbf_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                  ctypes.c_int, ctypes.c_size_t, ctypes.POINTER(ctypes.c_uint64)]),
+    "fbf_poll": (ctypes.c_int, [ctypes.c_uint64, _c_int_p]),
+    "fbf_wait": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_double]),
     "fbf_launch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "fbf_batch_capture": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "fbf_batch_replay": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)]),
-    "fbf_poll": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, _c_int_p]),
-    "fbf_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_double]),
+    "fbf_batch_poll": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, _c_int_p]),
+    "fbf_batch_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_double]),
     "fbf_batch_pending": (ctypes.c_int, [ctypes.c_void_p, _c_int_p]),
     "fbf_batch_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "fbf_filter_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
@@ -194,10 +199,29 @@ def fbf_batch_create(max_images: int, flags: int = 0) -> int:
     return h.value
 
 
-def fbf_submit(batch: int, plan: int, d_in: int, d_out: int, H: int, W: int, pitch_elems: int) -> int:
+def fbf_batch_submit(batch: int, plan: int, d_in: int, d_out: int, H: int, W: int, pitch_elems: int) -> int:
     t = ctypes.c_uint64()
-    _check(lib().fbf_submit(batch, plan, d_in, d_out, H, W, pitch_elems, ctypes.byref(t)), "fbf_submit")
+    _check(lib().fbf_batch_submit(batch, plan, d_in, d_out, H, W, pitch_elems, ctypes.byref(t)),
+           "fbf_batch_submit")
     return t.value
+
+
+def fbf_submit(plan: int, d_in: int, d_out: int, H: int, W: int, pitch_elems: int) -> int:
+    """Queue one image on the current device's implicit queue; returns its ticket."""
+    t = ctypes.c_uint64()
+    _check(lib().fbf_submit(plan, d_in, d_out, H, W, pitch_elems, ctypes.byref(t)), "fbf_submit")
+    return t.value
+
+
+def fbf_poll(ticket: int) -> int:
+    """FBF_DONE or FBF_PENDING for a ticket of fbf_submit (launching its queue if needed)."""
+    st = ctypes.c_int()
+    _check(lib().fbf_poll(ticket, ctypes.byref(st)), "fbf_poll")
+    return st.value
+
+
+def fbf_wait(ticket: int, timeout_s: float) -> None:
+    _check(lib().fbf_wait(ticket, timeout_s), "fbf_wait")
 
 
 def fbf_launch(batch: int, stream: int = 0) -> None:
@@ -214,14 +238,14 @@ def fbf_batch_replay(batch: int, stream: int = 0) -> int:
     return t.value
 
 
-def fbf_poll(batch: int, ticket: int) -> int:
+def fbf_batch_poll(batch: int, ticket: int) -> int:
     st = ctypes.c_int()
-    _check(lib().fbf_poll(batch, ticket, ctypes.byref(st)), "fbf_poll")
+    _check(lib().fbf_batch_poll(batch, ticket, ctypes.byref(st)), "fbf_batch_poll")
     return st.value
 
 
-def fbf_wait(batch: int, ticket: int, timeout_s: float) -> None:
-    _check(lib().fbf_wait(batch, ticket, timeout_s), "fbf_wait")
+def fbf_batch_wait(batch: int, ticket: int, timeout_s: float) -> None:
+    _check(lib().fbf_batch_wait(batch, ticket, timeout_s), "fbf_batch_wait")
 
 
 def fbf_batch_pending(batch: int) -> int:
@@ -462,7 +486,7 @@ class Batch:
             raise ValueError("x and y need unit column stride and equal row strides")
         self._keep.append(plan)
         H, W = x.shape
-        return fbf_submit(self.handle, plan.handle, x.data_ptr(), y.data_ptr(), H, W, x.stride(0))
+        return fbf_batch_submit(self.handle, plan.handle, x.data_ptr(), y.data_ptr(), H, W, x.stride(0))
 
     def launch(self, stream=None):
         import torch
@@ -482,10 +506,10 @@ class Batch:
         return fbf_batch_replay(self.handle, st.cuda_stream)
 
     def poll(self, ticket: int) -> int:
-        return fbf_poll(self.handle, ticket)
+        return fbf_batch_poll(self.handle, ticket)
 
     def wait(self, ticket: int, timeout_s: float = 60.0) -> None:
-        fbf_wait(self.handle, ticket, timeout_s)
+        fbf_batch_wait(self.handle, ticket, timeout_s)
 
     def pending(self) -> int:
         return fbf_batch_pending(self.handle)

@@ -1,11 +1,11 @@
 // Batched Fourier bilateral filtering: many images in one persistent launch.
 //
-// Images are queued with fbf_submit (host only), then fbf_launch groups them by radius
+// Images are queued with fbf_batch_submit (host only), then fbf_launch groups them by radius
 // class (the kernel instantiation that serves their r = ceil(3 theta)), uploads one device
 // work-list per class (per-image Work records and per-plan DeviceParams, one copy from a
 // pinned staging buffer) and starts one stream-K persistent kernel per class over the
 // concatenated (image, tile, term) sequence of the class.  An event recorded after the
-// launches marks the generation; tickets name a generation and fbf_poll / fbf_wait query
+// launches marks the generation; tickets name a generation and fbf_batch_poll / fbf_batch_wait query
 // it.  fbf_batch_capture records the same work as a CUDA graph (copy + kernels) that
 // fbf_batch_replay relaunches with the same pointers and sizes.
 //
@@ -203,7 +203,8 @@ void tune_store_locked(const std::string& key, const char* cfg) {
 
 // ---- the batch object ------------------------------------------------------------------------
 struct Pending {
-  const Plan* plan;
+  DeviceParams dp;                       // the plan's constants, copied at submit
+  int r, precision;
   const float* in;
   float* out;
   int H, W;
@@ -276,12 +277,12 @@ struct ClassPlan {
 int build_lists(Batch* b, std::vector<ClassPlan>* out, size_t* bytes) {
   std::map<int, ClassPlan> by;
   for (const Pending& pd : b->pending) {
-    const int cls = class_of(pd.plan->r, pd.plan->precision);
+    const int cls = class_of(pd.r, pd.precision);
     if (cls < 0) return set_error(FBF_EUNSUPPORTED, "fbf_batch: radius too large");
     ClassPlan& cp = by[cls];
     cp.cls = cls;
     // one DeviceParams per distinct plan in the class
-    const DeviceParams q = padded(pd.plan->dp, classes()[cls].rad);
+    const DeviceParams q = padded(pd.dp, classes()[cls].rad);
     int pidx = -1;
     for (size_t i = 0; i < cp.params.size() && pidx < 0; ++i)
       if (std::memcmp(&q, &cp.params[i], sizeof(DeviceParams)) == 0) pidx = (int)i;
@@ -295,7 +296,7 @@ int build_lists(Batch* b, std::vector<ClassPlan>* out, size_t* bytes) {
     w.pitch = (long long)pd.pitch;
     w.H = pd.H;
     w.W = pd.W;
-    w.K = pd.plan->dp.K;
+    w.K = pd.dp.K;
     w.wtile = 2 * w.K - 1;
     w.param_idx = pidx;
     cp.works.push_back(w);
@@ -536,7 +537,7 @@ int gen_status(Batch* b, unsigned long long g) {
   while (!b->gens.empty()) {
     cudaError_t e = cudaEventQuery(b->gens.front().ev);
     if (e == cudaErrorNotReady) break;
-    if (e != cudaSuccess) return set_error(FBF_ECUDA, std::string("fbf_poll: ") + cudaGetErrorString(e));
+    if (e != cudaSuccess) return set_error(FBF_ECUDA, std::string("fbf_batch_poll: ") + cudaGetErrorString(e));
     b->done_below = b->gens.front().id + 1;
     b->free_events.push_back(b->gens.front().ev);
     b->gens.erase(b->gens.begin());
@@ -547,7 +548,7 @@ int gen_status(Batch* b, unsigned long long g) {
       cudaError_t e = cudaEventQuery(gen.ev);
       if (e == cudaSuccess) return FBF_DONE;
       if (e == cudaErrorNotReady) return FBF_PENDING;
-      return set_error(FBF_ECUDA, std::string("fbf_poll: ") + cudaGetErrorString(e));
+      return set_error(FBF_ECUDA, std::string("fbf_batch_poll: ") + cudaGetErrorString(e));
     }
   }
   return FBF_DONE;
@@ -575,26 +576,26 @@ int fbf_batch_create(fbf_batch_t* out, int max_images, int flags) try {
   return FBF_OK;
 } FBF_ABI_CATCH("fbf_batch_create")
 
-int fbf_submit(fbf_batch_t batch, fbf_plan_t plan, const float* d_in, float* d_out, int H, int W,
+int fbf_batch_submit(fbf_batch_t batch, fbf_plan_t plan, const float* d_in, float* d_out, int H, int W,
                      size_t pitch_elems, fbf_ticket_t* ticket) try {
-  if (!batch || !plan) return fbf::set_error(FBF_EINVAL, "fbf_submit: NULL batch or plan");
-  if (!d_in || !d_out) return fbf::set_error(FBF_EINVAL, "fbf_submit: NULL image pointer");
-  if (H < 1 || W < 1) return fbf::set_error(FBF_EINVAL, "fbf_submit: H and W must be >= 1");
-  if (pitch_elems < (size_t)W) return fbf::set_error(FBF_EINVAL, "fbf_submit: pitch < W");
+  if (!batch || !plan) return fbf::set_error(FBF_EINVAL, "fbf_batch_submit: NULL batch or plan");
+  if (!d_in || !d_out) return fbf::set_error(FBF_EINVAL, "fbf_batch_submit: NULL image pointer");
+  if (H < 1 || W < 1) return fbf::set_error(FBF_EINVAL, "fbf_batch_submit: H and W must be >= 1");
+  if (pitch_elems < (size_t)W) return fbf::set_error(FBF_EINVAL, "fbf_batch_submit: pitch < W");
   const fbf::Plan* p = fbf::plan_of(plan);
   if (fbf::class_of(p->r, p->precision) < 0)
-    return fbf::set_error(FBF_EUNSUPPORTED, "fbf_submit: radius too large for the plan's form");
+    return fbf::set_error(FBF_EUNSUPPORTED, "fbf_batch_submit: radius too large for the plan's form");
   const size_t span = ((size_t)(H - 1) * pitch_elems + (size_t)W) * sizeof(float);
   const char* a = (const char*)d_in;
   const char* o = (const char*)d_out;
-  if (a < o + span && o < a + span) return fbf::set_error(FBF_EINVAL, "fbf_submit: in and out overlap");
+  if (a < o + span && o < a + span) return fbf::set_error(FBF_EINVAL, "fbf_batch_submit: in and out overlap");
   fbf::Batch& b = batch->b;
   std::lock_guard<std::mutex> lk(b.mu);
-  if ((int)b.pending.size() >= b.max_images) return fbf::set_error(FBF_EBUSY, "fbf_submit: batch is full");
-  b.pending.push_back({p, d_in, d_out, H, W, pitch_elems});
+  if ((int)b.pending.size() >= b.max_images) return fbf::set_error(FBF_EBUSY, "fbf_batch_submit: batch is full");
+  b.pending.push_back({p->dp, p->r, p->precision, d_in, d_out, H, W, pitch_elems});
   if (ticket) *ticket = (fbf_ticket_t)b.next_gen;
   return FBF_OK;
-} FBF_ABI_CATCH("fbf_submit")
+} FBF_ABI_CATCH("fbf_batch_submit")
 
 // Empties a batch's queue when the call that took its images returns, whether or not the
 // launch or capture succeeded: after an error the caller may free the images' buffers, so
@@ -682,19 +683,19 @@ int fbf_batch_replay(fbf_batch_t batch, void* cuda_stream, fbf_ticket_t* ticket)
   return FBF_OK;
 } FBF_ABI_CATCH("fbf_batch_replay")
 
-int fbf_poll(fbf_batch_t batch, fbf_ticket_t ticket, int* status) try {
-  if (!batch || !status) return fbf::set_error(FBF_EINVAL, "fbf_poll: NULL argument");
+int fbf_batch_poll(fbf_batch_t batch, fbf_ticket_t ticket, int* status) try {
+  if (!batch || !status) return fbf::set_error(FBF_EINVAL, "fbf_batch_poll: NULL argument");
   fbf::Batch& b = batch->b;
   std::lock_guard<std::mutex> lk(b.mu);
   const int s = fbf::gen_status(&b, (unsigned long long)ticket);
   if (s != FBF_DONE && s != FBF_PENDING) return s;
   *status = s;
   return FBF_OK;
-} FBF_ABI_CATCH("fbf_poll")
+} FBF_ABI_CATCH("fbf_batch_poll")
 
-int fbf_wait(fbf_batch_t batch, fbf_ticket_t ticket, double timeout_s) try {
-  if (!batch) return fbf::set_error(FBF_EINVAL, "fbf_wait: batch is NULL");
-  if (!(timeout_s >= 0)) return fbf::set_error(FBF_EINVAL, "fbf_wait: timeout must be >= 0");
+int fbf_batch_wait(fbf_batch_t batch, fbf_ticket_t ticket, double timeout_s) try {
+  if (!batch) return fbf::set_error(FBF_EINVAL, "fbf_batch_wait: batch is NULL");
+  if (!(timeout_s >= 0)) return fbf::set_error(FBF_EINVAL, "fbf_batch_wait: timeout must be >= 0");
   const auto t0 = std::chrono::steady_clock::now();
   while (true) {
     int s;
@@ -705,10 +706,10 @@ int fbf_wait(fbf_batch_t batch, fbf_ticket_t ticket, double timeout_s) try {
     if (s == FBF_DONE) return FBF_OK;
     if (s != FBF_PENDING) return s;
     const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-    if (el >= timeout_s) return fbf::set_error(FBF_ETIMEDOUT, "fbf_wait: timed out");
+    if (el >= timeout_s) return fbf::set_error(FBF_ETIMEDOUT, "fbf_batch_wait: timed out");
     std::this_thread::sleep_for(std::chrono::microseconds(50));
   }
-} FBF_ABI_CATCH("fbf_wait")
+} FBF_ABI_CATCH("fbf_batch_wait")
 
 int fbf_batch_pending(fbf_batch_t batch, int* n) try {
   if (!batch || !n) return fbf::set_error(FBF_EINVAL, "fbf_batch_pending: NULL argument");
@@ -737,5 +738,120 @@ int fbf_batch_destroy(fbf_batch_t batch) try {
   delete batch;
   return FBF_OK;
 } FBF_ABI_CATCH("fbf_batch_destroy")
+
+}  // extern "C"
+
+// ---- implicit per-device queue (fbf_submit / fbf_poll / fbf_wait) -----------------------------
+// One batch and one non-blocking stream per device, created on first use and kept until the
+// process exits.  A ticket carries its device: bits 48..55 hold device + 1, the low 48 bits
+// the batch generation.
+namespace fbf {
+namespace {
+
+constexpr int kImplicitMax = 4096;        // images per implicit launch
+constexpr int kTicketShift = 48;
+
+struct Implicit {
+  fbf_batch_s* batch = nullptr;
+  cudaStream_t st = nullptr;
+};
+std::mutex g_impl_mu;
+Implicit g_impl[64];
+
+// the implicit queue of device `dev` (created when `create`); nullptr with the error set
+Implicit* implicit_of(int dev, bool create, const char* who) {
+  if (dev < 0 || dev >= 64) {
+    set_error(FBF_EINVAL, std::string(who) + ": unknown ticket");
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lk(g_impl_mu);
+  Implicit& q = g_impl[dev];
+  if (!q.batch) {
+    if (!create) {
+      set_error(FBF_EINVAL, std::string(who) + ": unknown ticket");
+      return nullptr;
+    }
+    cudaStream_t st = nullptr;
+    const cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      set_error(FBF_ECUDA, std::string(who) + ": " + cudaGetErrorString(e));
+      return nullptr;
+    }
+    fbf_batch_t b = nullptr;
+    if (fbf_batch_create(&b, kImplicitMax, 0) != FBF_OK) {
+      cudaStreamDestroy(st);
+      return nullptr;
+    }
+    q.batch = b;
+    q.st = st;
+  }
+  return &q;
+}
+
+// launch the device's queue if the ticket's generation is still queued (on the device's
+// own stream, with that device current)
+int flush_for(Implicit* q, int dev, unsigned long long gen, const char* who) {
+  int cur = 0;
+  cudaError_t e = cudaGetDevice(&cur);
+  if (e != cudaSuccess) return set_error(FBF_ECUDA, std::string(who) + ": " + cudaGetErrorString(e));
+  int rc = FBF_OK;
+  bool queued;
+  {
+    std::lock_guard<std::mutex> lk(q->batch->b.mu);
+    queued = gen >= q->batch->b.next_gen;
+  }
+  if (queued) {
+    if (cur != dev && (e = cudaSetDevice(dev)) != cudaSuccess)
+      return set_error(FBF_ECUDA, std::string(who) + ": " + cudaGetErrorString(e));
+    rc = fbf_launch(q->batch, q->st);
+    if (cur != dev) cudaSetDevice(cur);
+  }
+  return rc;
+}
+
+}  // namespace
+}  // namespace fbf
+
+extern "C" {
+
+int fbf_submit(fbf_plan_t plan, const float* d_in, float* d_out, int H, int W, size_t pitch_elems,
+               fbf_ticket_t* ticket) try {
+  int dev = 0;
+  const cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fbf::set_error(FBF_ECUDA, std::string("fbf_submit: ") + cudaGetErrorString(e));
+  fbf::Implicit* q = fbf::implicit_of(dev, true, "fbf_submit");
+  if (!q) return FBF_ECUDA;
+  fbf_ticket_t t = 0;
+  int rc = fbf_batch_submit(q->batch, plan, d_in, d_out, H, W, pitch_elems, &t);
+  if (rc == FBF_EBUSY) {   // a full queue is launched and the image starts the next one
+    rc = fbf_launch(q->batch, q->st);
+    if (rc == FBF_OK) rc = fbf_batch_submit(q->batch, plan, d_in, d_out, H, W, pitch_elems, &t);
+  }
+  if (rc != FBF_OK) return rc;
+  if (ticket) *ticket = ((fbf_ticket_t)(dev + 1) << fbf::kTicketShift) | t;
+  return FBF_OK;
+} FBF_ABI_CATCH("fbf_submit")
+
+int fbf_poll(fbf_ticket_t ticket, int* status) try {
+  if (!status) return fbf::set_error(FBF_EINVAL, "fbf_poll: status is NULL");
+  const int dev = (int)(ticket >> fbf::kTicketShift) - 1;
+  const unsigned long long gen = ticket & ((1ull << fbf::kTicketShift) - 1);
+  fbf::Implicit* q = fbf::implicit_of(dev, false, "fbf_poll");
+  if (!q) return FBF_EINVAL;
+  int rc = fbf::flush_for(q, dev, gen, "fbf_poll");
+  if (rc != FBF_OK) return rc;
+  return fbf_batch_poll(q->batch, gen, status);
+} FBF_ABI_CATCH("fbf_poll")
+
+int fbf_wait(fbf_ticket_t ticket, double timeout_s) try {
+  if (!(timeout_s >= 0)) return fbf::set_error(FBF_EINVAL, "fbf_wait: timeout must be >= 0");
+  const int dev = (int)(ticket >> fbf::kTicketShift) - 1;
+  const unsigned long long gen = ticket & ((1ull << fbf::kTicketShift) - 1);
+  fbf::Implicit* q = fbf::implicit_of(dev, false, "fbf_wait");
+  if (!q) return FBF_EINVAL;
+  int rc = fbf::flush_for(q, dev, gen, "fbf_wait");
+  if (rc != FBF_OK) return rc;
+  return fbf_batch_wait(q->batch, gen, timeout_s);
+} FBF_ABI_CATCH("fbf_wait")
 
 }  // extern "C"

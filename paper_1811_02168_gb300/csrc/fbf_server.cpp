@@ -7,7 +7,7 @@
 //              from the server's own stream-ordered memory pool and the image is copied in
 //              at once on the upload stream;
 //   launch     whenever fewer than max_inflight launches are in flight, everything admitted
-//              so far goes into one batched launch (fbf_submit / fbf_launch: one persistent
+//              so far goes into one batched launch (fbf_batch_submit / fbf_launch: one persistent
 //              stream-K kernel per precision form and radius class) on the compute stream,
 //              after the uploads it needs (events); requests that arrive meanwhile join the
 //              next launch instead of waiting for a fixed batch;
@@ -148,7 +148,7 @@ int launch(fbf_server_s* s, Launch& L) {
   for (Req* r : L.reqs) {
     e = cudaStreamWaitEvent(s->comp, r->up, 0);
     if (e != cudaSuccess) return fbf::set_error(FBF_ECUDA, std::string("fbf_server: ") + cudaGetErrorString(e));
-    const int rc = fbf_submit(s->batch, r->plan, r->d_in, r->d_out, r->H, r->W, (size_t)r->W, nullptr);
+    const int rc = fbf_batch_submit(s->batch, r->plan, r->d_in, r->d_out, r->H, r->W, (size_t)r->W, nullptr);
     if (rc != FBF_OK) return rc;
   }
   int rc = fbf_launch(s->batch, s->comp);
@@ -231,7 +231,7 @@ void worker_main(fbf_server_s* s) {
       lk.lock();
       if (rc != FBF_OK) {
         // the stream state is unknown: wait for what was enqueued, free what was not freed.
-        // fbf_launch empties the batch's queue on failure too; if an fbf_submit failed
+        // fbf_launch empties the batch's queue on failure too; if an fbf_batch_submit failed
         // before it, images stay queued, and the batch (idle now) is made anew
         lk.unlock();
         release_after_error(s, L.reqs);

@@ -49,6 +49,8 @@ def test_binding_constants_equal_the_header():
     for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
         for m in re.finditer(r"^#define\s+(FBF_\w+)\s+\(?(\d+)u?(?:\s*<<\s*(\d+))?\)?", open(h).read(), flags=re.M):
             defined[m.group(1)] = int(m.group(2)) << int(m.group(3) or 0)
+        for m in re.finditer(r"^#define\s+(FBF_\w+)\s+(FBF_\w+)\s*$", open(h).read(), flags=re.M):
+            defined[m.group(1)] = defined[m.group(2)]   # another name for a defined constant
     mirrored = {n: getattr(B, n) for n in dir(B) if n.startswith("FBF_") and isinstance(getattr(B, n), int)}
     assert {"FBF_OK", "FBF_EINVAL", "FBF_EUNSUPPORTED", "FBF_FP32", "FBF_BF16_TC", "FBF_MAX_K"} <= set(mirrored)
     unknown = sorted(set(mirrored) - set(defined))
@@ -188,28 +190,57 @@ def test_batch_host_side_queue_and_bounded_wait():
     p = B.Plan(30.0, 255, 3.0, K=4)
     b = B.fbf_batch_create(2, 0)
     try:
-        t0 = B.fbf_submit(b, p.handle, 1 << 20, 1 << 30, 16, 16, 16)
-        t1 = B.fbf_submit(b, p.handle, 1 << 21, 1 << 31, 8, 9, 9)
+        t0 = B.fbf_batch_submit(b, p.handle, 1 << 20, 1 << 30, 16, 16, 16)
+        t1 = B.fbf_batch_submit(b, p.handle, 1 << 21, 1 << 31, 8, 9, 9)
         assert t0 == t1                       # same pending launch
         assert B.fbf_batch_pending(b) == 2
         with pytest.raises(B.FbfError) as ei:
-            B.fbf_submit(b, p.handle, 1 << 22, 1 << 32, 4, 4, 4)
+            B.fbf_batch_submit(b, p.handle, 1 << 22, 1 << 32, 4, 4, 4)
         assert ei.value.code == B.FBF_EBUSY
         for kw in (dict(d_in=0), dict(H=0), dict(pitch_elems=2)):
             args = dict(d_in=1 << 23, d_out=1 << 33, H=4, W=4, pitch_elems=4)
             args.update(kw)
             with pytest.raises(B.FbfError) as ei:
-                B.fbf_submit(b, p.handle, args["d_in"], args["d_out"], args["H"], args["W"],
-                             args["pitch_elems"])
+                B.fbf_batch_submit(b, p.handle, args["d_in"], args["d_out"], args["H"], args["W"],
+                                   args["pitch_elems"])
             assert ei.value.code in (B.FBF_EINVAL, B.FBF_EBUSY)
-        assert B.fbf_poll(b, t0) == B.FBF_PENDING
+        assert B.fbf_batch_poll(b, t0) == B.FBF_PENDING
         with pytest.raises(B.FbfError) as ei:
-            B.fbf_wait(b, t0, 0.05)
+            B.fbf_batch_wait(b, t0, 0.05)
         assert ei.value.code == B.FBF_ETIMEDOUT
     finally:
         B.fbf_batch_destroy(b)
     with pytest.raises(B.FbfError):
         B.fbf_batch_create(0, 0)
+
+
+def test_implicit_queue_host_side():
+    """fbf_submit / fbf_poll / fbf_wait (no batch handle): a ticket that no fbf_submit
+    returned is refused on the host; without a GPU, fbf_submit reports the CUDA failure
+    instead of queueing."""
+    for bad in (0, 5, (70 << 48) | 1):
+        with pytest.raises(B.FbfError) as ei:
+            B.fbf_poll(bad)
+        assert ei.value.code == B.FBF_EINVAL
+        with pytest.raises(B.FbfError) as ei:
+            B.fbf_wait(bad, 0.01)
+        assert ei.value.code == B.FBF_EINVAL
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        return
+    p = B.Plan(30.0, 255, 3.0, K=4)
+    with pytest.raises(B.FbfError) as ei:
+        B.fbf_submit(p.handle, 1 << 20, 1 << 30, 16, 16, 16)
+    assert ei.value.code == B.FBF_ECUDA
+
+
+def test_precision_names_of_the_problem_statement():
+    """FBF_BF16 and FBF_TF32_TC name the compensated BF16 / TF32 tensor-core form."""
+    hdr = open(os.path.join(ROOT, "include", "fbf.h")).read()
+    assert "#define FBF_BF16       FBF_BF16_TC" in hdr and "#define FBF_TF32_TC    FBF_BF16_TC" in hdr
+    assert B.FBF_BF16 == B.FBF_TF32_TC == B.FBF_BF16_TC
+    p = B.Plan(30.0, 255, 3.0, K=4, precision=B.FBF_TF32_TC)
+    assert p.K == 4
 
 
 def test_failed_launch_empties_the_queue():
@@ -223,7 +254,7 @@ def test_failed_launch_empties_the_queue():
     b = B.fbf_batch_create(2, 0)
     try:
         for call in (lambda: B.fbf_launch(b, 0), lambda: B.fbf_batch_capture(b, 0)):
-            B.fbf_submit(b, p.handle, 1 << 20, 1 << 30, 16, 16, 16)
+            B.fbf_batch_submit(b, p.handle, 1 << 20, 1 << 30, 16, 16, 16)
             assert B.fbf_batch_pending(b) == 1
             with pytest.raises(B.FbfError):
                 call()

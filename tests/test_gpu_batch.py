@@ -315,3 +315,39 @@ def test_autotune_cache_file(B, tmp_path):
     run()
     last = cache.read_text().strip().split("\n")[-1].split()
     assert last[0] == key15 and last[1].startswith("r15_ty")
+
+
+def test_implicit_queue_submit_and_poll(B):
+    """fbf_submit / fbf_poll without a batch handle: images queued on the device's implicit
+    queue are launched together at the first poll and equal fbf_filter; plans may be
+    destroyed right after submitting (their parameters are copied); one image against the
+    oracle."""
+    jobs = _mixed_jobs(5, 33)
+    items, tickets = [], []
+    torch.cuda.synchronize()
+    for H, W, theta, sigma, K, seed in jobs:
+        plan = B.Plan(sigma, 255, theta, K=K)
+        x = torch.from_numpy(voronoi_image(H, W, 8, 30.0, 10.0, seed=seed)).cuda()
+        y = torch.full_like(x, -1.0)
+        torch.cuda.synchronize()
+        tickets.append(B.fbf_submit(plan.handle, x.data_ptr(), y.data_ptr(), H, W, W))
+        items.append((H, W, theta, sigma, K, x, y))
+        plan.close()
+    assert len(set(tickets)) == 1          # one launch for the whole queue
+    B.fbf_wait(tickets[-1], 60.0)
+    assert B.fbf_poll(tickets[0]) == B.FBF_DONE
+    for H, W, theta, sigma, K, x, y in items:
+        assert _close(y, _single(B, B.Plan(sigma, 255, theta, K=K), x))
+    H, W, theta, sigma, K, x, y = items[0]
+    op = ofit.make_plan(sigma, 255, K=K)
+    ref = ofl.fourier_bf(x.cpu().numpy().astype(np.float64), theta, op.c, op.T)
+    assert np.abs(y.cpu().numpy() - ref).max() <= TOL
+    # a second round on the same queue gets a new ticket
+    H, W, theta, sigma, K, x, y = items[1]
+    plan = B.Plan(sigma, 255, theta, K=K)
+    y2 = torch.full_like(x, -1.0)
+    t2 = B.fbf_submit(plan.handle, x.data_ptr(), y2.data_ptr(), H, W, W)
+    assert t2 != tickets[0]
+    while B.fbf_poll(t2) != B.FBF_DONE:
+        pass
+    assert torch.equal(y2, y)
