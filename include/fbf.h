@@ -412,7 +412,8 @@ const char* fbf_last_error(void);
  * that a bounded wait for a TMA copy of the f halo in the FP32 kernel gave up; in either
  * case that launch's output is incomplete.  Read it after synchronising the stream of the
  * launches in question.  Clearing a nonzero word also resets the library's cached
- * split-tile counters (synchronising the devices that hold them). */
+ * split-tile counters (synchronising the devices that hold them); a batch (fbf_batch_t) one
+ * of whose launches gave up keeps its own counters and is to be destroyed and made anew. */
 int fbf_device_errors(int* flags, int clear);
 
 /* fbf_debug_fp32_peak -- measurement aid, not part of the method: launch a probe of the
@@ -425,6 +426,17 @@ int fbf_device_errors(int* flags, int clear);
  * iters >= 1, else FBF_EINVAL; launch errors FBF_ECUDA. */
 int fbf_debug_fp32_peak(int pairs, int blocks, int threads, long long iters, float* d_out,
                         void* cuda_stream, double* flop);
+
+/* fbf_debug_set_wait_limit -- test aid, not part of the method: with polls > 0, the bounded
+ * waits inside the kernels' own pipelines on the current device (the FP32 single-image
+ * kernel's wait for a TMA box of the f halo; the tensor-core kernels' mbarrier waits between
+ * their roles) become `polls` non-blocking polls, so that a test can make them give up and
+ * exercise the abort path: the launch leaves its output incomplete, reports the bit in
+ * fbf_device_errors, and first lets every copy and MMA it started complete (those final
+ * waits keep their full limits) and frees its tensor memory.  polls = 0 restores the
+ * normal limits.  Affects launches made after the call.  Errors: FBF_EINVAL (polls < 0),
+ * FBF_ECUDA. */
+int fbf_debug_set_wait_limit(int polls);
 
 /* fbf_version -- library version string. */
 const char* fbf_version(void);

@@ -113,6 +113,7 @@ SIGNATURES = {
     "fbf_device_errors": (ctypes.c_int, [_c_int_p, ctypes.c_int]),
     "fbf_last_error": (ctypes.c_char_p, []),
     "fbf_version": (ctypes.c_char_p, []),
+    "fbf_debug_set_wait_limit": (ctypes.c_int, [ctypes.c_int]),
     "fbf_debug_fp32_peak": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_longlong,
                                            ctypes.c_void_p, ctypes.c_void_p, _c_double_p]),
     "fbf_debug_error_curve": (ctypes.c_int, [_c_double_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -379,6 +380,11 @@ def fbf_last_error() -> str:
 
 def fbf_version() -> str:
     return lib().fbf_version().decode()
+
+
+def fbf_debug_set_wait_limit(polls: int) -> None:
+    """Test aid: make the kernels' pipeline waits give up after `polls` polls (0 = normal)."""
+    _check(lib().fbf_debug_set_wait_limit(polls), "fbf_debug_set_wait_limit")
 
 
 def fbf_debug_fp32_peak(pairs: bool, blocks: int, threads: int, iters: int, d_out: int, stream) -> float:

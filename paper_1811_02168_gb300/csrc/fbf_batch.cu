@@ -37,28 +37,41 @@ using namespace fp32;
 
 // ---- kernel configurations per radius class --------------------------------------------
 struct ClassLaunch {
-  // launches the batched kernel of one configuration; returns FBF_OK or an error code
+  // launches the batched kernel of one configuration; returns FBF_OK or an error code.
+  // carry / kmax: the carried-row slots (configurations with carry_bytes_per_term) and the
+  // largest K of the work-list
   int (*launch)(const DeviceParams* dparams, const Work* dwork, int n, long long wtot,
-                float* partial, int* counter, cudaStream_t st, int dev);
+                float* partial, int* counter, float2* carry, int kmax, cudaStream_t st, int dev);
   // partial-sum bytes one launch of this configuration needs (per CTA slots) on dev
   int (*partial_bytes)(int dev, size_t* out);
+  // carried-row bytes per cosine term of the longest image (0: rows are not carried)
+  int (*carry_bytes_per_term)(int dev, size_t* out);
   int TY;
   const char* name;
   int TX = fp32::TX;   // tile width of the kernel's schedule
 };
 
-template <int RAD, int TY, int NT, int NY>
+int no_carry(int, size_t* out) {
+  *out = 0;
+  return FBF_OK;
+}
+
+template <int RAD, int TY, int NT, int NY, bool CARRY>
 struct BatchCfg {
   using C = Cfg<RAD, TY, NT, NY>;
+  static constexpr auto kernel() {
+    if constexpr (CARRY) return &fbf_fp32_batch_carry_kernel<RAD, TY, NT, NY>;
+    else return &fbf_fp32_batch_kernel<RAD, TY, NT, NY>;
+  }
   static int sms[64], occ[64];
+  static std::mutex mu;
   static int slots(int dev, int* G) {
+    std::lock_guard<std::mutex> lk(mu);
     if (!occ[dev]) {
-      cudaError_t e = cudaFuncSetAttribute(fbf_fp32_batch_kernel<RAD, TY, NT, NY>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM_BYTES);
+      cudaError_t e = cudaFuncSetAttribute(kernel(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM_BYTES);
       if (e != cudaSuccess) return set_error(FBF_ECUDA, std::string("fbf_batch: ") + cudaGetErrorString(e));
       int n = 0;
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fbf_fp32_batch_kernel<RAD, TY, NT, NY>, NT,
-                                                        C::SMEM_BYTES);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel(), NT, C::SMEM_BYTES);
       if (e != cudaSuccess || n < 1) return set_error(FBF_ECUDA, "fbf_batch: kernel does not fit on an SM");
       int s = 0;
       cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev);
@@ -75,8 +88,15 @@ struct BatchCfg {
     *out = (size_t)G * 2 * 2 * NY * NT * sizeof(float);
     return FBF_OK;
   }
+  static int carry_bytes_per_term(int dev, size_t* out) {
+    int G = 0;
+    int rc = slots(dev, &G);
+    if (rc != FBF_OK) return rc;
+    *out = CARRY ? (size_t)G * 2 * carry_rows(RAD, 4) * TX * sizeof(float2) : 0;
+    return FBF_OK;
+  }
   static int launch(const DeviceParams* dparams, const Work* dwork, int n, long long wtot,
-                    float* partial, int* counter, cudaStream_t st, int dev) {
+                    float* partial, int* counter, float2* carry, int kmax, cudaStream_t st, int dev) {
     int G = 0;
     int rc = slots(dev, &G);
     if (rc != FBF_OK) return rc;
@@ -86,18 +106,22 @@ struct BatchCfg {
     sc.wtot = wtot;
     sc.partial = partial;
     sc.counter = counter;
-    fbf_fp32_batch_kernel<RAD, TY, NT, NY><<<(unsigned)g, NT, C::SMEM_BYTES, st>>>(dparams, dwork, n, sc);
+    sc.carry = carry;
+    sc.kmax = kmax;
+    kernel()<<<(unsigned)g, NT, C::SMEM_BYTES, st>>>(dparams, dwork, n, sc);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return set_error(FBF_ECUDA, std::string("fbf_batch: ") + cudaGetErrorString(e));
     return FBF_OK;
   }
 };
-template <int RAD, int TY, int NT, int NY> int BatchCfg<RAD, TY, NT, NY>::sms[64] = {0};
-template <int RAD, int TY, int NT, int NY> int BatchCfg<RAD, TY, NT, NY>::occ[64] = {0};
+template <int RAD, int TY, int NT, int NY, bool CARRY> int BatchCfg<RAD, TY, NT, NY, CARRY>::sms[64] = {0};
+template <int RAD, int TY, int NT, int NY, bool CARRY> int BatchCfg<RAD, TY, NT, NY, CARRY>::occ[64] = {0};
+template <int RAD, int TY, int NT, int NY, bool CARRY> std::mutex BatchCfg<RAD, TY, NT, NY, CARRY>::mu;
 
-template <int RAD, int TY, int NT, int NY>
-constexpr ClassLaunch cfg_entry(const char* name) {
-  return ClassLaunch{&BatchCfg<RAD, TY, NT, NY>::launch, &BatchCfg<RAD, TY, NT, NY>::partial_bytes, TY, name};
+template <int RAD, int TY, int NT, int NY, bool CARRY = false>
+ClassLaunch cfg_entry(const char* name) {
+  using B = BatchCfg<RAD, TY, NT, NY, CARRY>;
+  return ClassLaunch{&B::launch, &B::partial_bytes, &B::carry_bytes_per_term, TY, name};
 }
 
 struct RadClass {
@@ -109,12 +133,12 @@ struct RadClass {
 // tensor-core forms: one configuration per (radius class, precision), 128 x 64 tiles
 template <int RAD, int PREC>
 int tc_launch(const DeviceParams* dparams, const Work* dwork, int n, long long wtot, float* partial, int* counter,
-              cudaStream_t st, int dev) {
+              float2*, int, cudaStream_t st, int dev) {
   return launch_tc_batch(RAD, PREC, dparams, dwork, n, wtot, partial, counter, st, dev);
 }
 template <int RAD, int PREC>
 ClassLaunch tc_entry(const char* name) {
-  ClassLaunch c{&tc_launch<RAD, PREC>, &tc_batch_partial_bytes, tc_tile_rows(RAD, PREC), name};
+  ClassLaunch c{&tc_launch<RAD, PREC>, &tc_batch_partial_bytes, &no_carry, tc_tile_rows(RAD, PREC), name};
   c.TX = 128;
   return c;
 }
@@ -125,9 +149,10 @@ const std::vector<RadClass>& classes() {
       {6, {cfg_entry<6, 112, 512, 7>("r6_ty112_nt512"), cfg_entry<6, 128, 256, 16>("r6_ty128_nt256")}},
       {9, {cfg_entry<9, 96, 512, 6>("r9_ty96_nt512")}},
       {15, {cfg_entry<15, 96, 512, 6>("r15_ty96_nt512"), cfg_entry<15, 128, 256, 16>("r15_ty128_nt256")}},
-      {24, {cfg_entry<24, 128, 256, 16>("r24_ty128_nt256")}},
-      {30, {cfg_entry<30, 128, 256, 16>("r30_ty128_nt256"), cfg_entry<30, 96, 256, 12>("r30_ty96_nt256")}},
-      {48, {cfg_entry<48, 64, 128, 16>("r48_ty64_nt128")}},
+      {24, {cfg_entry<24, 128, 256, 16, true>("r24_ty128_nt256_carry"), cfg_entry<24, 128, 256, 16>("r24_ty128_nt256")}},
+      {30, {cfg_entry<30, 128, 256, 16, true>("r30_ty128_nt256_carry"), cfg_entry<30, 128, 256, 16>("r30_ty128_nt256"),
+            cfg_entry<30, 96, 256, 12>("r30_ty96_nt256")}},
+      {48, {cfg_entry<48, 64, 128, 16, true>("r48_ty64_nt128_carry"), cfg_entry<48, 64, 128, 16>("r48_ty64_nt128")}},
       {6, {tc_entry<6, FBF_FP16_TC>("tc_fp16_r6")}, FBF_FP16_TC},
       {15, {tc_entry<15, FBF_FP16_TC>("tc_fp16_r15")}, FBF_FP16_TC},
       {30, {tc_entry<30, FBF_FP16_TC>("tc_fp16_r30")}, FBF_FP16_TC},
@@ -359,25 +384,45 @@ int ensure_buffers(Batch* b, size_t list_bytes, size_t counters, size_t partial,
     e = cudaEventCreateWithFlags(&lb.copied, cudaEventDisableTiming);
     if (e != cudaSuccess) return set_error(FBF_ECUDA, std::string("fbf_batch: ") + cudaGetErrorString(e));
   }
+  // Buffers grow rarely (at least 1 MiB of work-lists, then doubling): a regrowth waits for
+  // the work that may still read the old buffer -- the graph's replays may run on any stream
+  // (the device), a launch's on its own stream (launches of a batch are ordered).
+  const bool graph_slot = b->slot == Batch::kRing;
+  auto drain_old = [&]() { return graph_slot ? cudaDeviceSynchronize() : cudaStreamSynchronize(st); };
   if (lb.cap < list_bytes) {
     drop_graph_if_owned(b);
+    if (lb.d) {
+      e = drain_old();
+      if (e != cudaSuccess) return set_error(FBF_ECUDA, std::string("fbf_batch: ") + cudaGetErrorString(e));
+      cudaFree(lb.d);
+    }
     if (lb.h) cudaFreeHost(lb.h);
-    if (lb.d) { cudaDeviceSynchronize(); cudaFree(lb.d); }
     lb.h = lb.d = nullptr;
+    const size_t cap = std::max(2 * list_bytes, (size_t)1 << 20);
     lb.cap = 0;
-    e = cudaMallocHost(&lb.h, list_bytes);
-    if (e != cudaSuccess) return set_error(FBF_ENOMEM, std::string("fbf_batch: ") + cudaGetErrorString(e));
-    e = cudaMalloc(&lb.d, list_bytes);
-    if (e != cudaSuccess) return set_error(FBF_ENOMEM, std::string("fbf_batch: ") + cudaGetErrorString(e));
-    lb.cap = list_bytes;
+    e = cudaMallocHost(&lb.h, cap);
+    if (e != cudaSuccess) {
+      lb.h = nullptr;
+      return set_error(FBF_ENOMEM, std::string("fbf_batch: ") + cudaGetErrorString(e));
+    }
+    e = cudaMalloc(&lb.d, cap);
+    if (e != cudaSuccess) {
+      lb.d = nullptr;
+      return set_error(FBF_ENOMEM, std::string("fbf_batch: ") + cudaGetErrorString(e));
+    }
+    lb.cap = cap;
   }
   Batch::ScratchBuf& sb = cur_scratch(b);
   if (sb.counter_cap < counters || sb.partial_cap < partial) {
     drop_graph_if_owned(b);
-    if (sb.d) { cudaDeviceSynchronize(); cudaFree(sb.d); }
+    if (sb.d) {
+      e = drain_old();
+      if (e != cudaSuccess) return set_error(FBF_ECUDA, std::string("fbf_batch: ") + cudaGetErrorString(e));
+      cudaFree(sb.d);
+    }
     sb.d = nullptr;
     sb.counter_cap = sb.partial_cap = 0;
-    const size_t cc = std::max(counters + counters / 2, (size_t)1024);
+    const size_t cc = std::max(2 * counters, (size_t)1 << 16);
     const size_t pc = partial + partial / 2;
     const size_t cbytes = ((cc * sizeof(int) + 255) / 256) * 256;
     e = cudaMalloc(&sb.d, cbytes + pc);
@@ -410,6 +455,18 @@ void write_lists(Batch* b, const std::vector<ClassPlan>& cps) {
   }
 }
 
+// scratch bytes of one class launch: its partial sums (256-byte aligned, `part`) and, for a
+// configuration that carries x-pass rows, the slots for kmax terms after them (`total`)
+int class_scratch_bytes(const ClassLaunch& cl, int dev, int kmax, size_t* part, size_t* total) {
+  size_t pb = 0, cb = 0;
+  int rc = cl.partial_bytes(dev, &pb);
+  if (rc == FBF_OK) rc = cl.carry_bytes_per_term(dev, &cb);
+  if (rc != FBF_OK) return rc;
+  *part = (pb + 255) / 256 * 256;
+  *total = *part + cb * (size_t)kmax;
+  return FBF_OK;
+}
+
 int launch_classes(Batch* b, const std::vector<ClassPlan>& cps, size_t list_bytes, cudaStream_t st,
                    bool capturing) {
   Batch::ListBuf& lb = b->ring[b->slot];
@@ -423,9 +480,15 @@ int launch_classes(Batch* b, const std::vector<ClassPlan>& cps, size_t list_byte
   char* d = static_cast<char*>(lb.d);
   for (const ClassPlan& cp : cps) {
     const ClassLaunch& cl = classes()[cp.cls].cands[cp.cand];
-    int rc = cl.launch(reinterpret_cast<const DeviceParams*>(d + cp.params_off),
-                       reinterpret_cast<const Work*>(d + cp.work_off), (int)cp.works.size(), cp.wtot,
-                       scratch_partials(b), scratch_counters(b), st, b->dev);
+    size_t part = 0, total = 0;
+    int rc = class_scratch_bytes(cl, b->dev, cp.kmax, &part, &total);
+    if (rc != FBF_OK) return rc;
+    // the class's carried-row slots follow its partial sums (classes run one after another)
+    float2* carry = total > part ? reinterpret_cast<float2*>(reinterpret_cast<char*>(scratch_partials(b)) + part)
+                                 : nullptr;
+    rc = cl.launch(reinterpret_cast<const DeviceParams*>(d + cp.params_off),
+                   reinterpret_cast<const Work*>(d + cp.work_off), (int)cp.works.size(), cp.wtot,
+                   scratch_partials(b), scratch_counters(b), carry, cp.kmax, st, b->dev);
     if (rc != FBF_OK) return rc;
   }
   return FBF_OK;
@@ -457,8 +520,8 @@ int prepare(Batch* b, std::vector<ClassPlan>* cps, size_t* list_bytes, cudaStrea
         for (size_t j = 0; j < cands.size(); ++j) {
           ClassPlan one = cp;
           layout(one, (int)j);
-          size_t pb = 0;
-          rc = cands[j].partial_bytes(b->dev, &pb);
+          size_t part = 0, pb = 0;
+          rc = class_scratch_bytes(cands[j], b->dev, one.kmax, &part, &pb);
           if (rc != FBF_OK) return rc;
           rc = ensure_buffers(b, *list_bytes, (size_t)one.tiles, pb, st);
           if (rc != FBF_OK) return rc;
@@ -493,8 +556,8 @@ int prepare(Batch* b, std::vector<ClassPlan>* cps, size_t* list_bytes, cudaStrea
       }
     }
     layout(cp, choice);
-    size_t pb = 0;
-    rc = cands[choice].partial_bytes(b->dev, &pb);
+    size_t part = 0, pb = 0;
+    rc = class_scratch_bytes(cands[choice], b->dev, cp.kmax, &part, &pb);
     if (rc != FBF_OK) return rc;
     counters = std::max(counters, (size_t)cp.tiles);
     partial = std::max(partial, pb);
@@ -606,6 +669,7 @@ struct EmptyQueueOnExit {
 };
 
 int fbf_launch(fbf_batch_t batch, void* cuda_stream) try {
+  const fbf::NvtxRange tr("fbf_launch");
   if (!batch) return fbf::set_error(FBF_EINVAL, "fbf_launch: batch is NULL");
   fbf::Batch& b = batch->b;
   std::lock_guard<std::mutex> lk(b.mu);
@@ -629,6 +693,7 @@ int fbf_launch(fbf_batch_t batch, void* cuda_stream) try {
 } FBF_ABI_CATCH("fbf_launch")
 
 int fbf_batch_capture(fbf_batch_t batch, void* cuda_stream) try {
+  const fbf::NvtxRange tr("fbf_batch_capture");
   if (!batch) return fbf::set_error(FBF_EINVAL, "fbf_batch_capture: batch is NULL");
   fbf::Batch& b = batch->b;
   std::lock_guard<std::mutex> lk(b.mu);
@@ -669,6 +734,7 @@ int fbf_batch_capture(fbf_batch_t batch, void* cuda_stream) try {
 } FBF_ABI_CATCH("fbf_batch_capture")
 
 int fbf_batch_replay(fbf_batch_t batch, void* cuda_stream, fbf_ticket_t* ticket) try {
+  const fbf::NvtxRange tr("fbf_batch_replay");
   if (!batch) return fbf::set_error(FBF_EINVAL, "fbf_batch_replay: batch is NULL");
   fbf::Batch& b = batch->b;
   std::lock_guard<std::mutex> lk(b.mu);

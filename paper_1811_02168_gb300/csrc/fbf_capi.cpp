@@ -116,6 +116,7 @@ extern "C" {
 
 int fbf_plan(fbf_plan_t* out, double sigma, int R, double theta, int K, double eps,
              int precision, int flags) try {
+  const fbf::NvtxRange tr("fbf_plan");
   if (!(sigma > 0) || !std::isfinite(sigma)) {
     if (out) *out = nullptr;
     return fbf::set_error(FBF_EINVAL, "fbf_plan: sigma must be > 0");
@@ -166,6 +167,7 @@ int fbf_plan_destroy(fbf_plan_t plan) try {
 
 int fbf_filter(fbf_plan_t plan, const float* d_in, float* d_out, int H, int W,
                size_t pitch_elems, void* cuda_stream) try {
+  const fbf::NvtxRange tr("fbf_filter");
   if (!plan) return fbf::set_error(FBF_EINVAL, "fbf_filter: plan is NULL");
   if (!d_in || !d_out) return fbf::set_error(FBF_EINVAL, "fbf_filter: NULL image pointer");
   if (H < 1 || W < 1) return fbf::set_error(FBF_EINVAL, "fbf_filter: H and W must be >= 1");
@@ -210,6 +212,14 @@ int fbf_device_errors(int* flags, int clear) try {
 } FBF_ABI_CATCH("fbf_device_errors")
 
 // Test hook: E(K,T) for K = 1..Kc at one T from the C++ fitter (host only).
+int fbf_debug_set_wait_limit(int polls) try {
+  fbf::clear_error();
+  if (polls < 0) return fbf::set_error(FBF_EINVAL, "fbf_debug_set_wait_limit: polls must be >= 0");
+  int rc = fbf::fp32_set_wait_polls(polls);
+  if (rc == FBF_OK) rc = fbf::tc_set_wait_polls(polls);
+  return rc;
+} FBF_ABI_CATCH("fbf_debug_set_wait_limit")
+
 int fbf_debug_error_curve(const double* b, int R, int T, int Kc, double* E_out) try {
   if (!b || !E_out || R < 1 || T < 1 || Kc < 1) return fbf::set_error(FBF_EINVAL, "bad argument");
   fbf::kernel_error_curve(b, R, T, Kc, E_out);

@@ -118,6 +118,13 @@ int reset_workspace_counters() {
   return FBF_OK;
 }
 
+// Test hook of the single-image FP32 kernels' TMA wait (fbf_debug_set_wait_limit).
+int fp32_set_wait_polls(int polls) {
+  const cudaError_t e = cudaMemcpyToSymbol(fp32::g_fp32_wait_polls, &polls, sizeof(int));
+  if (e != cudaSuccess) return set_error(FBF_ECUDA, std::string("fbf_debug_set_wait_limit: ") + cudaGetErrorString(e));
+  return FBF_OK;
+}
+
 // The FP32 device error word of this translation unit's kernels (the single-image ones).
 int fp32_device_errors(int* flags, int clear) {
   int v = 0;
@@ -277,7 +284,10 @@ int launch_cfg(const DeviceParams& dp, const float* in, float* out, int H, int W
   const size_t carry_bytes = carry ? (size_t)G * dp.K * CSLOT * sizeof(float2) : 0;
   rc = get_workspace(dev, st, align256(partial_bytes) + carry_bytes, (size_t)w.tiles, &sc.partial, &sc.counter);
   if (rc != FBF_OK) return rc;
-  if (carry) sc.carry = reinterpret_cast<float2*>(reinterpret_cast<char*>(sc.partial) + align256(partial_bytes));
+  if (carry) {
+    sc.carry = reinterpret_cast<float2*>(reinterpret_cast<char*>(sc.partial) + align256(partial_bytes));
+    sc.kmax = dp.K;
+  }
   bool launched = false;
   if constexpr (C::TMA_OK) {
     if (tma) {

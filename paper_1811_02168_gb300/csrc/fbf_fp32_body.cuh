@@ -48,12 +48,45 @@ __device__ __forceinline__ void tma_load_box(float* dst, const CUtensorMap* map,
                " [%0], [%1, {%2, %3}], [%4];"
                :: "r"(smem_addr(dst)), "l"(map), "r"(x), "r"(y), "r"(smem_addr(bar)) : "memory");
 }
-// 16-byte asynchronous copy global -> shared (completed by cp.async.wait_all)
-__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" :: "r"(smem_addr(smem_dst)), "l"(gsrc) : "memory");
+// L2 policies for the carried rows: a slot is rewritten one tile later, so its lines are
+// kept in L2 ahead of streaming data (evict_last); a slot read for the last time is marked
+// evict_first and its lines discarded (dead data is not written back to DRAM).
+__device__ __forceinline__ unsigned long long l2_policy_keep() {
+  unsigned long long pol;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
 }
-__device__ __forceinline__ bool tma_bar_wait(unsigned long long* bar, uint32_t parity) {
+__device__ __forceinline__ unsigned long long l2_policy_drop() {
+  unsigned long long pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+// 16-byte asynchronous copy global -> shared with an L2 policy (completed by cp.async.wait_all)
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc, unsigned long long pol) {
+  asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;"
+               :: "r"(smem_addr(smem_dst)), "l"(gsrc), "l"(pol) : "memory");
+}
+__device__ __forceinline__ void st_global_v4(void* p, float4 v, unsigned long long pol) {
+  asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;"
+               :: "l"(p), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "l"(pol) : "memory");
+}
+// invalidate the 128-byte L2 line at p (its contents become undefined; nothing is written back)
+__device__ __forceinline__ void l2_discard_line(const void* p) {
+  asm volatile("discard.global.L2 [%0], 128;" :: "l"(p) : "memory");
+}
+__device__ __forceinline__ bool tma_bar_wait(unsigned long long* bar, uint32_t parity, int polls = 0) {
   const uint32_t a = smem_addr(bar);
+  if (polls > 0) {   // test hook: that many non-blocking polls
+    for (int it = 0; it < polls; ++it) {
+      uint32_t done;
+      asm volatile(
+          "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+          " selp.u32 %0, 1, 0, p;\n}"
+          : "=r"(done) : "r"(a), "r"(parity) : "memory");
+      if (done) return true;
+    }
+    return false;
+  }
   unsigned long long t0 = 0;
   for (int it = 0; it < kTmaWaitLimit; ++it) {
     uint32_t done;
@@ -75,6 +108,10 @@ __device__ __forceinline__ bool tma_bar_wait(unsigned long long* bar, uint32_t p
 // Device error word of the FP32 kernels (bit 1: a TMA wait gave up; that launch's output is
 // incomplete).  Each translation unit has its own copy; the single-image launcher reads its own.
 static __device__ int g_fp32_error;
+// Test hook (fbf_debug_set_wait_limit): > 0 makes the wait for a tile's TMA box give up after
+// that many non-blocking polls (the wait for the copy in flight before leaving keeps its full
+// limit); 0 = normal limits.  Per translation unit, like the error word.
+static __device__ int g_fp32_wait_polls;
 
 // largest divisor of rows_per_warp whose group keeps at most 24 loads per lane in flight
 __host__ __device__ constexpr int stage_group(int rows_per_warp, int cols_per_lane) {
@@ -139,7 +176,8 @@ struct Scratch {
   long long wtot;                     // total weight of the launch
   float* partial;                     // G * 2 slots * 2 * NY * NT floats
   int* counter;                       // one per tile of every image, zero between launches
-  float2* carry;                      // carried x-pass rows (SingleSrcCarry): G * K slots
+  float2* carry;                      // carried x-pass rows (carry sources): G * kmax slots
+  int kmax;                           // largest K of the launch's images (carry slots per CTA)
 };
 
 // A single image whose parameters sit in the constant bank (kernel parameter).
@@ -192,10 +230,12 @@ struct SingleSrcCarry {
 // of the row-group height (4 rows for k >= 1, 8 for k = 0) not above 2r
 __host__ __device__ constexpr int carry_rows(int rad, int group) { return (2 * rad) / group * group; }
 
-// A device work-list of images (batched launch).
-struct ListSrc {
+// A device work-list of images (batched launch); with CARRY, each image's tiles are numbered
+// down its strips and x-pass rows are carried as for SingleSrcCarry, within one image.
+template <bool CARRY = false>
+struct ListSrcT {
   static constexpr bool kTma = false;
-  static constexpr bool kCarry = false;
+  static constexpr bool kCarry = CARRY;
   const DeviceParams* __restrict__ prm;
   const Work* __restrict__ wl;
   int n;
@@ -212,6 +252,7 @@ struct ListSrc {
     return lo;
   }
 };
+using ListSrc = ListSrcT<false>;
 
 __device__ __forceinline__ long long ceil_div_ll(long long a, long long b) { return (a + b - 1) / b; }
 
@@ -370,6 +411,7 @@ __device__ __forceinline__ void fbf_body(const Src& src, const Scratch& sc) {
   // one while the tile before it is filtered
   uint32_t fph = 0;   // phase parity to wait for, per buffer
   int fb = 0;         // buffer of the current tile
+  const int wait_polls = TMA ? g_fp32_wait_polls : 0;
   if constexpr (TMA) {
     if (tid == 0) {
       tma_bar_init(fbar);
@@ -422,7 +464,7 @@ __device__ __forceinline__ void fbf_body(const Src& src, const Scratch& sc) {
     if constexpr (TMA) {
       // this tile's box was requested by the previous tile (or above); NaN marks outside pixels
       const uint32_t par = (fph >> fb) & 1u;
-      const bool got = tma_bar_wait(fbar + fb, par);
+      const bool got = tma_bar_wait(fbar + fb, par, wait_polls);
       fph ^= 1u << fb;
       if (__syncthreads_or(!got)) {
         // gave up: record it, let the copy in flight land (bounded), and leave
@@ -507,13 +549,16 @@ __device__ __forceinline__ void fbf_body(const Src& src, const Scratch& sc) {
       // are generated and convolved
       const int cs = (k == 0) ? CS0 : CS1;
       const int ncs = ((k == 0) ? 1 : 2) * cs * (TX / 2);   // 16-byte chunks
-      const bool carried = CARRY && tyi > 0 && (t - 1) * K + k >= u_first;
-      float2* const slot = CARRY ? sc.carry + ((long long)c * K + k) * CSLOT : nullptr;
+      const bool carried = CARRY && tyi > 0 && (img != img_first || (t - 1) * K + k >= u_first);
+      // the tile below takes rows from this one when this CTA filters its term k too
+      const bool keeps = CARRY && tyi + 1 < wk.tiles_y && (img < img_end || (t + 1) * K + k < u_end);
+      float2* const slot = CARRY ? sc.carry + ((long long)c * sc.kmax + k) * CSLOT : nullptr;
       if (CARRY && carried) {
+        const unsigned long long pol = keeps ? l2_policy_keep() : l2_policy_drop();
         for (int i = tid; i < ncs; i += NT) {
           const int cp = i / (cs * (TX / 2)), rem = i - cp * cs * (TX / 2);
           const int row = rem / (TX / 2), col = (rem - row * (TX / 2)) * 2;
-          cp_async16(hbuf + cp * C::CPS + row * C::HS2 + col, slot + (cp * CS1 + row) * TX + col);
+          cp_async16(hbuf + cp * C::CPS + row * C::HS2 + col, slot + (cp * CS1 + row) * TX + col, pol);
         }
       }
       const int xr0 = carried ? cs : 0;
@@ -591,12 +636,20 @@ __device__ __forceinline__ void fbf_body(const Src& src, const Scratch& sc) {
       // rows [TY, TY + cs) are rows [0, cs) of the next tile of the strip: keep them for it
       // when this CTA filters its term k (same chunk per thread as the load above, so each
       // thread rereads only what it wrote itself)
-      if (CARRY && tyi + 1 < wk.tiles_y && (img < img_end || (t + 1) * K + k < u_end)) {
+      if (CARRY && keeps) {
+        const unsigned long long pol = l2_policy_keep();
         for (int i = tid; i < ncs; i += NT) {
           const int cp = i / (cs * (TX / 2)), rem = i - cp * cs * (TX / 2);
           const int row = rem / (TX / 2), col = (rem - row * (TX / 2)) * 2;
-          *reinterpret_cast<float4*>(slot + (cp * CS1 + row) * TX + col) =
-              *reinterpret_cast<const float4*>(hbuf + cp * C::CPS + (TY + row) * C::HS2 + col);
+          st_global_v4(slot + (cp * CS1 + row) * TX + col,
+                       *reinterpret_cast<const float4*>(hbuf + cp * C::CPS + (TY + row) * C::HS2 + col), pol);
+        }
+      } else if (CARRY && carried) {
+        // read for the last time (every thread's copies completed before the barrier above)
+        for (int i = tid * 8; i < ncs; i += NT * 8) {
+          const int cp = i / (cs * (TX / 2)), rem = i - cp * cs * (TX / 2);
+          const int row = rem / (TX / 2), col = (rem - row * (TX / 2)) * 2;
+          l2_discard_line(slot + (cp * CS1 + row) * TX + col);
         }
       }
       // the next term's table goes to the other buffer while this term's is still read
@@ -704,7 +757,7 @@ __device__ __forceinline__ void fbf_body(const Src& src, const Scratch& sc) {
         if (gy < H && gx < W) {
           const float d = den[a];
           const float f = fh[(oy + a + RAD) * FS + ox + RAD];
-          out[(long)gy * pitch + gx] = (d > 0.f) ? m + num[a] / d : f;
+          __stcs(out + (long)gy * pitch + gx, (d > 0.f) ? m + num[a] / d : f);   // streamed
         }
       }
     }
@@ -748,6 +801,15 @@ fbf_fp32_batch_kernel(const DeviceParams* __restrict__ params, const Work* __res
   fbf_body<RAD, TY, NT, NY>(src, sc);
 }
 
+
+// A device work-list of images sharing one radius class, x-pass rows carried down each strip.
+template <int RAD, int TY, int NT, int NY>
+__global__ void __launch_bounds__(NT, 1)
+fbf_fp32_batch_carry_kernel(const DeviceParams* __restrict__ params, const Work* __restrict__ work,
+                            int n, const Scratch sc) {
+  const ListSrcT<true> src{params, work, n};
+  fbf_body<RAD, TY, NT, NY>(src, sc);
+}
 
 // padded copy of a plan's parameters for the RAD instantiation (taps beyond the plan's
 // radius are zero, so a wider instantiation serves a smaller r)

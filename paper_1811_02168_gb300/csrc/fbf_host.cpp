@@ -96,6 +96,7 @@ int prepare(HostCtx& c, size_t n) {
 
 extern "C" int fbf_filter_host(fbf_plan_t plan, const float* host_in, float* host_out, int H, int W,
                                size_t pitch_elems, void* cuda_stream) try {
+  const fbf::NvtxRange tr("fbf_filter_host");
   if (!plan) return fbf::set_error(FBF_EINVAL, "fbf_filter_host: plan is NULL");
   if (!host_in || !host_out) return fbf::set_error(FBF_EINVAL, "fbf_filter_host: NULL image pointer");
   if (H < 1 || W < 1) return fbf::set_error(FBF_EINVAL, "fbf_filter_host: H and W must be >= 1");

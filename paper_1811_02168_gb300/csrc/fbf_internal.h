@@ -10,6 +10,8 @@
 
 #include "fbf.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 struct CUstream_st;
 using cudaStream_t_ = CUstream_st*;
 
@@ -70,6 +72,17 @@ struct Plan {
 // the Plan behind a C handle (defined with the handle type in fbf_capi.cpp)
 const Plan* plan_of(fbf_plan_t h);
 
+// ---- tracing ----------------------------------------------------------------------------
+// An NVTX range over a host-side stage (plan, launch, serving admission and completion), so
+// that a timeline of a process using the library shows where the host time goes.  Without
+// a tool attached, a push/pop costs a call to an empty function.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 // ---- errors ---------------------------------------------------------------------------
 int set_error(int code, const std::string& msg);
 
@@ -105,6 +118,9 @@ int device_errors(int* flags, int clear);
 // FP32 single-image kernels' error word (bit 1: a TMA wait gave up), and the reset of the
 // cached split-tile counters that a launch which gave up part way leaves nonzero.
 int fp32_device_errors(int* flags, int clear);
+// Test hook: poll limit of the kernels' pipeline waits (0 = normal limits), per kernel family.
+int fp32_set_wait_polls(int polls);
+int tc_set_wait_polls(int polls);
 int reset_workspace_counters();
 
 // batched tensor-core launch of one radius class (6, 15 or 30) from a device work-list

@@ -123,6 +123,7 @@ void release_after_error(fbf_server_s* s, const std::vector<Req*>& reqs) {
 
 // Device buffers and the upload of one admitted request (called without the lock).
 int upload(fbf_server_s* s, Req* r) {
+  const fbf::NvtxRange tr("fbf_server admit: upload");
   const size_t n = (size_t)r->H * r->W * sizeof(float);
   void* a = nullptr;
   void* b = nullptr;
@@ -144,6 +145,7 @@ int upload(fbf_server_s* s, Req* r) {
 // One batched launch of the admitted requests, the downloads and the releases behind it
 // (called without the lock).
 int launch(fbf_server_s* s, Launch& L) {
+  const fbf::NvtxRange tr("fbf_server launch");
   cudaError_t e = cudaSuccess;
   for (Req* r : L.reqs) {
     e = cudaStreamWaitEvent(s->comp, r->up, 0);
@@ -256,6 +258,7 @@ void worker_main(fbf_server_s* s) {
       Launch& L = s->inflight.front();
       const cudaError_t q = cudaEventQuery(L.done);
       if (q == cudaErrorNotReady) break;
+      const fbf::NvtxRange tr("fbf_server complete");
       const double t = now_s();
       const int st = (q == cudaSuccess) ? FBF_DONE : FBF_ECUDA;
       if (st != FBF_DONE) fbf::set_error(FBF_ECUDA, std::string("fbf_server: ") + cudaGetErrorString(q));

@@ -54,6 +54,9 @@ using fp32::locate;
 using fp32::term_cs_any;
 
 __device__ int g_tc_error;   // bit 0: an mbarrier wait gave up
+// Test hook (fbf_debug_set_wait_limit): > 0 makes the role waits give up after that many
+// non-blocking polls (the final drain of the MMAs keeps its full limit); 0 = normal limits.
+__device__ int g_tc_wait_polls;
 
 constexpr int TILE_X = 128;             // output tile width  = TMEM lanes = MMA M
 constexpr int TILE_Y_MAX = 64;          // output tile height = y-pass N (per configuration: TcCfg::TY)
@@ -122,7 +125,7 @@ struct TcCfg {
   static_assert(SMEM <= 232448, "tensor-core tile does not fit in shared memory");
   static_assert(KY <= 256, "x-pass N exceeds one MMA");
   static_assert(NC * CK == KS, "chunking");
-  static_assert(2 * NSLOT + 8 <= BARB / 8 - 2, "barrier space");
+  static_assert(2 * NSLOT + 8 <= BARB / 8 - 2, "barrier space (then four ints: TMEM base, abort, finish, polls)");
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -251,11 +254,23 @@ __device__ __forceinline__ uint64_t global_ns() {
 // Bounded wait for phase `parity` of an mbarrier.  Each poll may suspend the thread (up to
 // kSuspendNs, woken early when the phase completes), so waiting warps take no issue slots.
 // Gives up (false) after kWaitLimit polls or kWaitNs of wall time, or early once the CTA's
-// abort flag is raised (when `flag` is given).
+// abort flag is raised (when `flag` is given: flag[0] the abort flag, flag[2] the test
+// hook's poll limit, which turns the wait into that many non-blocking polls).
 constexpr uint32_t kSuspendNs = 1000000;
 constexpr uint64_t kWaitNs = 2000000000ull;
 __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, const volatile int* flag) {
   const uint32_t a = smem_u32(mbar);
+  if (flag && flag[2] > 0) {
+    for (int it = 0; it < flag[2]; ++it) {
+      uint32_t done;
+      asm volatile(
+          "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+          " selp.u32 %0, 1, 0, p;\n}"
+          : "=r"(done) : "r"(a), "r"(parity) : "memory");
+      if (done) return true;
+    }
+    return false;
+  }
   uint64_t t0 = 0;
   for (int it = 0; it < kWaitLimit; ++it) {
     uint32_t done;
@@ -569,6 +584,7 @@ __device__ __forceinline__ void tc_body(const Src& src, const Scratch& sc) {
   uint32_t* sTmem = reinterpret_cast<uint32_t*>(bars + 8 + 2 * C::NSLOT);
   volatile int* sAbort = reinterpret_cast<volatile int*>(sTmem + 1);
   volatile int* sFin = sAbort + 1;
+  volatile int* sPolls = sAbort + 2;   // test hook's poll limit (see mbar_wait)
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
@@ -584,6 +600,7 @@ __device__ __forceinline__ void tc_body(const Src& src, const Scratch& sc) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(bRb)), "r"(NCW));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(bDrain)));
     *sAbort = 0;
+    *sPolls = g_tc_wait_polls;
   }
   proxy_fence();
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -1076,6 +1093,12 @@ int tc_batch_partial_bytes(int dev, size_t* out) {
   cudaError_t e = cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return set_error(FBF_ECUDA, std::string("fbf_launch: ") + cudaGetErrorString(e));
   *out = (size_t)s * 2 * 2 * tc::PX_MAX * tc::NCT * sizeof(float);
+  return FBF_OK;
+}
+
+int tc_set_wait_polls(int polls) {
+  const cudaError_t e = cudaMemcpyToSymbol(tc::g_tc_wait_polls, &polls, sizeof(int));
+  if (e != cudaSuccess) return set_error(FBF_ECUDA, std::string("fbf_debug_set_wait_limit: ") + cudaGetErrorString(e));
   return FBF_OK;
 }
 

@@ -316,3 +316,14 @@ def test_filter_host_argument_errors():
     assert L.fbf_filter_host(p.handle, a, a, 8, 8, 7, None) == B.FBF_EINVAL       # pitch < W
     assert L.fbf_filter_host(p.handle, a, a + 4, 8, 8, 8, None) == B.FBF_EINVAL   # partial overlap
 
+
+
+def test_nvtx_ranges_on_the_host_stages():
+    """Host-side stages carry NVTX ranges (plan, filter, host call, batch launch / capture /
+    replay, serving admission, launch and completion) for timeline tools."""
+    src = ""
+    for f in glob.glob(os.path.join(ROOT, "paper_1811_02168_gb300", "csrc", "*.c*")):
+        src += open(f).read()
+    for name in ("fbf_plan", "fbf_filter", "fbf_filter_host", "fbf_launch", "fbf_batch_capture",
+                 "fbf_batch_replay", "fbf_server admit: upload", "fbf_server launch", "fbf_server complete"):
+        assert f'NvtxRange tr("{name}")' in src, name

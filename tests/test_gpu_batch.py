@@ -350,4 +350,29 @@ def test_implicit_queue_submit_and_poll(B):
     assert t2 != tickets[0]
     while B.fbf_poll(t2) != B.FBF_DONE:
         pass
-    assert torch.equal(y2, y)
+    assert _close(y2, y)   # alone in its launch: only the split-tile partial sums are cut elsewhere
+
+
+def test_batch_carries_rows_for_wide_radii(B):
+    """Radius classes above 15 run the work-list kernel that carries x-pass rows down each
+    image's strips (one carry slot per CTA and term of the longest image): tall images of
+    different K in one launch equal their lone launches, and one matches the oracle."""
+    specs = [(1500, 700, 10.0, 30.0, 4), (900, 1300, 10.0, 80.0, 8), (2100, 400, 8.0, 10.0, 16),
+             (600, 600, 16.0, 30.0, 3)]
+    batch = B.Batch(8)
+    items = []
+    for i, (H, W, theta, sigma, K) in enumerate(specs):
+        plan = B.Plan(sigma, 255, theta, K=K)
+        x = torch.from_numpy(voronoi_image(H, W, 80, 40.0, 12.0, seed=700 + i)).cuda()
+        y = torch.full_like(x, -1.0)
+        batch.submit(plan, x, y)
+        items.append((plan, x, y))
+    batch.launch()
+    torch.cuda.synchronize()
+    for plan, x, y in items:
+        assert _close(y, _single(B, plan, x))
+    plan, x, y = items[0]
+    op = ofit.make_plan(plan.sigma, 255, K=plan.K)
+    ref = ofl.fourier_bf(x.cpu().numpy().astype(np.float64), plan.theta, op.c, op.T)
+    assert np.abs(y.cpu().numpy() - ref).max() <= TOL
+    batch.close()

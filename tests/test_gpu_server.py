@@ -109,3 +109,30 @@ def test_errors(B):
     with pytest.raises(B.FbfError):
         srv.poll(12345)
     srv.close()
+
+
+@pytest.mark.parametrize("form,tol", [("fp32", TOL), ("bf16_tc", 0.5)])
+def test_served_in_a_mix_matches_the_oracle(B, form, tol):
+    """Requests served in shared launches with others (bursts of ten) are compared element
+    by element with the FP64 Fourier oracle at the form's tolerance (relative to the output's
+    magnitude beyond [0, 255], as for the other served-path checks)."""
+    from oracle import fit as ofit
+    from oracle import filters as ofl
+    prec = {"fp32": B.FBF_FP32, "bf16_tc": B.FBF_BF16_TC}[form]
+    reqs = _requests(30, 8)
+    hin = [torch.from_numpy(r["img"]).pin_memory() for r in reqs]
+    hout = [torch.full((r["H"], r["W"]), -1.0).pin_memory() for r in reqs]
+    srv = B.Server(precision=prec, hbm_budget_bytes=1 << 30, max_batch=8, max_inflight=2)
+    srv.replay([r["t"] for r in reqs], hin, hout, [r["theta"] for r in reqs], [r["sigma"] for r in reqs],
+               [r["K"] for r in reqs])
+    srv.drain(120.0)
+    st = srv.stats()
+    srv.close()
+    assert st["requests"] == len(reqs) and st["launches"] < len(reqs)
+    for i in (0, 7, 13, 22):
+        r = reqs[i]
+        op = ofit.make_plan(r["sigma"], 255, K=r["K"])
+        ref = ofl.fourier_bf(r["img"].astype(np.float64), r["theta"], op.c, op.T)
+        scale = max(1.0, float(np.abs(ref).max()) / 255.0)
+        err = float(np.abs(hout[i].numpy() - ref).max())
+        assert err <= tol * scale, (i, r["H"], r["W"], r["theta"], r["sigma"], r["K"], err)
