@@ -120,3 +120,20 @@ def test_tc_non_gaussian_range_kernel(B, form):
     ref = ofl.fourier_bf(img.astype(np.float64), 3.0, op.c, op.T)
     assert float(np.abs(_run(B, plan, img) - ref).max()) <= TOL[form]
     assert B.fbf_device_errors() == 0
+
+
+@pytest.mark.parametrize("noninteger", [False, True])
+def test_bf16_wide_radius_half_row_items(B, noninteger):
+    """The compensated form at r = 30 generates its one-K-step operand chunks as half
+    core-matrix rows (4 pixels per thread, all compute threads busy): a ragged 333 x 457 image
+    (border tiles with masked pixels), 8-bit or with non-integer values (the general phase
+    path), against the oracle."""
+    img = voronoi_image(333, 457, 30, 40.0, 12.0, seed=41)
+    if noninteger:
+        rng = np.random.default_rng(42)
+        img = (img * 0.9 + rng.uniform(0.0, 0.999, img.shape)).astype(np.float32)
+    plan = B.Plan(30.0, 255, 10.0, K=6, precision=B.FBF_BF16_TC)
+    op = ofit.make_plan(30.0, 255, K=6)
+    ref = ofl.fourier_bf(img.astype(np.float64), 10.0, op.c, op.T)
+    assert float(np.abs(_run(B, plan, img) - ref).max()) <= TOL["bf16"]
+    assert B.fbf_device_errors() == 0
