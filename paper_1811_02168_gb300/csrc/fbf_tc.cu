@@ -86,8 +86,14 @@ struct TcCfg {
   static constexpr int KY = (HY + 15) / 16 * 16;          // x-pass N = y-pass K
   static constexpr int GYB = TY * KY * 4;                 // Gy, TF32 (shared memory)
   static constexpr int GY16B = NPART == 2 ? TY * KY * 2 : 0;   // Gy, FP16: the lo part's y pass
-  static constexpr int GLB = NPART == 2 ? TILE_X * KX * 2 : 0;   // Gx_lo (shared memory)
-  static constexpr int GXHB = GX_SMEM ? TILE_X * KX * 2 : 0;     // Gx (hi) in shared memory
+  // Gx in shared memory is kept as one tall band: the x pass's A block of K-step s,
+  // Gx[x', 16 s + j] = g(16 s + j - x'), is rows [16 (KS - 1 - s), +128) of
+  // U[y, j] = g(j - y + 16 (KS - 1)), y < GXU rows (a banded Toeplitz matrix repeats itself
+  // shifted by 16 rows per K-step), so the descriptor of step s starts 2 (KS - 1 - s) row
+  // groups into U instead of a TILE_X x KX copy
+  static constexpr int GXU = TILE_X + 16 * (KX / 16 - 1);          // rows of the band U
+  static constexpr int GLB = NPART == 2 ? GXU * 16 * 2 : 0;       // Gx_lo band (shared memory)
+  static constexpr int GXHB = GX_SMEM ? GXU * 16 * 2 : 0;         // Gx (hi) band in shared memory
   // B_h is produced as NC column chunks of CK x-pass K-steps (16 columns each) into a ring of
   // NSLOT chunk slots, each holding the chunk of both images of a pair (and of both parts of
   // the compensated form), with its own full / empty barriers: generation runs ahead of the
@@ -522,31 +528,34 @@ __device__ __forceinline__ void load_taps(const DeviceParams& p, unsigned char* 
                      pack2<__half>(v[6], v[7]));
     }
   }
+  // the Gx bands U[y, j] = g(j - y + 16 (KS - 1)) (see TcCfg::GXU): lo parts (compensated
+  // form) and, at r > 15, hi parts
+  constexpr int SH = C::KX - 16;   // 16 (KS - 1)
   if (NPART == 2) {
-    for (int i = tid; i < TILE_X * (C::KX / 8); i += NCT) {
-      const int o = i / (C::KX / 8), k8 = (i - o * (C::KX / 8)) * 8;
+    for (int i = tid; i < C::GXU * 2; i += NCT) {
+      const int y = i >> 1, k8 = (i & 1) * 8;
       float v[8];
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
-        const int d = k8 + j - o;
+        const int d = k8 + j - y + SH;
         const float gv = (d >= 0 && d <= 2 * RAD) ? p.g[d] : 0.f;
         v[j] = gv - round16<T>(gv);
       }
-      *reinterpret_cast<uint4*>(sGl + off16<C::KX>(o, k8)) =
+      *reinterpret_cast<uint4*>(sGl + off16<16>(y, k8)) =
           make_uint4(pack2<T>(v[0], v[1]), pack2<T>(v[2], v[3]), pack2<T>(v[4], v[5]), pack2<T>(v[6], v[7]));
     }
   }
   if (C::GX_SMEM) {
     unsigned char* sGxh = sGl + C::GLB;
-    for (int i = tid; i < TILE_X * (C::KX / 8); i += NCT) {
-      const int o = i / (C::KX / 8), k8 = (i - o * (C::KX / 8)) * 8;
+    for (int i = tid; i < C::GXU * 2; i += NCT) {
+      const int y = i >> 1, k8 = (i & 1) * 8;
       float v[8];
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
-        const int d = k8 + j - o;
+        const int d = k8 + j - y + SH;
         v[j] = (d >= 0 && d <= 2 * RAD) ? p.g[d] : 0.f;
       }
-      *reinterpret_cast<uint4*>(sGxh + off16<C::KX>(o, k8)) =
+      *reinterpret_cast<uint4*>(sGxh + off16<16>(y, k8)) =
           make_uint4(pack2<T>(v[0], v[1]), pack2<T>(v[2], v[3]), pack2<T>(v[4], v[5]), pack2<T>(v[6], v[7]));
     }
   }
@@ -647,8 +656,10 @@ __device__ __forceinline__ void tc_body(const Src& src, const Scratch& sc) {
       const uint64_t dGy = op_desc(smem_u32(sGy), 32 * C::KY);
       const uint64_t dGy16 = op_desc(smem_u32(sGy + C::GYB), 16 * C::KY);
       const uint64_t dBh = op_desc(smem_u32(sBh), 16 * C::CW);
-      const uint64_t dGl = op_desc(smem_u32(sGl), 16 * C::KX);
-      const uint64_t dGxh = op_desc(smem_u32(sGl + C::GLB), 16 * C::KX);
+      // Gx bands: K-step ks starts 2 (KS - 1 - ks) row groups (512 bytes each step) into U
+      const uint64_t dGl = op_desc(smem_u32(sGl), 256);
+      const uint64_t dGxh = op_desc(smem_u32(sGl + C::GLB), 256);
+      constexpr int KSL = C::KX / 16 - 1;
       uint32_t P = 0;
       int slot0 = 0, ring0 = 0;        // ring slot and use count of the next chunk
       bool ab = false;
@@ -677,13 +688,13 @@ __device__ __forceinline__ void tc_body(const Src& src, const Scratch& sc) {
                 const uint64_t bhi = dBh + (uint64_t)((slot0 * C::SLOTB + s * C::CB + kk * 256) >> 4);
                 const uint64_t blo = bhi + (uint64_t)((2 * C::CB) >> 4);
                 if (C::GX_SMEM) {
-                  mma_ss_el(tmem + C::D1C + s * C::D1S, dGxh + (uint64_t)(16 * ks), bhi, idX, ks > 0 ? 1u : 0u);
-                  mma_ss_el(tmem + C::D1C + s * C::D1S, dGxh + (uint64_t)(16 * ks), blo, idX, 1u);
+                  mma_ss_el(tmem + C::D1C + s * C::D1S, dGxh + (uint64_t)(32 * (KSL - ks)), bhi, idX, ks > 0 ? 1u : 0u);
+                  mma_ss_el(tmem + C::D1C + s * C::D1S, dGxh + (uint64_t)(32 * (KSL - ks)), blo, idX, 1u);
                 } else {
                   mma_ts_f16(tmem + C::D1C + s * C::D1S, tmem + C::GXC + 8 * ks, bhi, idX, ks > 0 ? 1u : 0u);
                   if (NPART == 2) mma_ts_f16(tmem + C::D1C + s * C::D1S, tmem + C::GXC + 8 * ks, blo, idX, 1u);
                 }
-                if (NPART == 2) mma_ss_el(tmem + C::D1C + s * C::D1S, dGl + (uint64_t)(16 * ks), bhi, idX, 1u);
+                if (NPART == 2) mma_ss_el(tmem + C::D1C + s * C::D1S, dGl + (uint64_t)(32 * (KSL - ks)), bhi, idX, 1u);
               }
               if (c == C::NC - 1) mma_commit_el(s ? bXb : bXa);
             }
