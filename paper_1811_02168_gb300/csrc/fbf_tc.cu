@@ -97,10 +97,13 @@ struct TcCfg {
   // B_h is produced as NC column chunks of CK x-pass K-steps (16 columns each) into a ring of
   // NSLOT chunk slots, each holding the chunk of both images of a pair (and of both parts of
   // the compensated form), with its own full / empty barriers: generation runs ahead of the
-  // x pass by up to NSLOT chunks
+  // x pass by up to NSLOT chunks.  (Compensated form at r = 30: two-K-step chunks, three
+  // slots; one-K-step chunks with seven slots were 3.89 against 3.21 ms at 4096^2: every
+  // chunk hand-off costs a round trip between the roles, and a one-K-step chunk holds fewer
+  // eight-pixel rows than there are compute threads.)
   static constexpr int KS = KX / 16;
   static constexpr int CK = NPART == 1 ? (KS % 4 == 0 ? 4 : KS % 3 == 0 ? 3 : KS % 5 == 0 ? 5 : KS % 2 == 0 ? 2 : 1)
-                                       : GX_SMEM ? 1 : (KS % 2 == 0 ? 2 : KS % 3 == 0 ? 3 : 1);
+                                       : GX_SMEM ? (KS % 2 == 0 ? 2 : 1) : (KS % 2 == 0 ? 2 : KS % 3 == 0 ? 3 : 1);
   static constexpr int NC = KS / CK;
   static constexpr int CW = 16 * CK;                      // chunk columns
   static constexpr int CB = KY * CW * 2;                  // bytes of one image part's chunk (16-bit)
