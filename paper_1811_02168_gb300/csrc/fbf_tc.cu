@@ -94,20 +94,6 @@ struct TcCfg {
   static constexpr int GXU = TILE_X + 16 * (KX / 16 - 1);          // rows of the band U
   static constexpr int GLB = NPART == 2 ? GXU * 16 * 2 : 0;       // Gx_lo band (shared memory)
   static constexpr int GXHB = GX_SMEM ? GXU * 16 * 2 : 0;         // Gx (hi) band in shared memory
-  // B_h is produced as NC column chunks of CK x-pass K-steps (16 columns each) into a ring of
-  // NSLOT chunk slots, each holding the chunk of both images of a pair (and of both parts of
-  // the compensated form), with its own full / empty barriers: generation runs ahead of the
-  // x pass by up to NSLOT chunks.  (Compensated form at r = 30: two-K-step chunks, three
-  // slots; one-K-step chunks with seven slots were 3.89 against 3.21 ms at 4096^2: every
-  // chunk hand-off costs a round trip between the roles, and a one-K-step chunk holds fewer
-  // eight-pixel rows than there are compute threads.)
-  static constexpr int KS = KX / 16;
-  static constexpr int CK = NPART == 1 ? (KS % 4 == 0 ? 4 : KS % 3 == 0 ? 3 : KS % 5 == 0 ? 5 : KS % 2 == 0 ? 2 : 1)
-                                       : GX_SMEM ? (KS % 2 == 0 ? 2 : 1) : (KS % 2 == 0 ? 2 : KS % 3 == 0 ? 3 : 1);
-  static constexpr int NC = KS / CK;
-  static constexpr int CW = 16 * CK;                      // chunk columns
-  static constexpr int CB = KY * CW * 2;                  // bytes of one image part's chunk (16-bit)
-  static constexpr int SLOTB = 2 * NPART * CB;            // a chunk slot: [a, b] per part
   static constexpr int FHS = KX + 8;                      // f-halo row stride (bytes)
   static constexpr int FHB = (KY * FHS + 127) / 128 * 128;
   static constexpr int GENW = 256 * NPART;                // words of one pair's operand table
@@ -115,6 +101,25 @@ struct TcCfg {
   static constexpr int TABB = 2 * TABW * 4;               // 2 slots (terms k even / odd)
   static constexpr int BARB = 256;
   static constexpr int FIXED = GYB + GY16B + GLB + GXHB + FHB + TABB + BARB + 1024;
+  // B_h is produced as NC column chunks of CK x-pass K-steps (16 columns each) into a ring of
+  // NSLOT chunk slots, each holding the chunk of both images of a pair (and of both parts of
+  // the compensated form), with its own full / empty barriers: generation runs ahead of the
+  // x pass by up to NSLOT chunks.  CK is the largest divisor of the K-step count that leaves
+  // room for two slots: every chunk hand-off costs a round trip between the roles (the
+  // compensated form at r = 30 at 4096^2: 1-, 2- and 3-K-step chunks with 7, 3 and 2 slots
+  // took 3.89, 3.21 and 3.13 ms).
+  static constexpr int KS = KX / 16;
+  static constexpr int slot_bytes(int ck) { return 2 * NPART * KY * 16 * ck * 2; }
+  static constexpr int pick_ck() {
+    for (int ck = KS; ck > 1; --ck)
+      if (KS % ck == 0 && (232448 - FIXED) / slot_bytes(ck) >= 2) return ck;
+    return 1;
+  }
+  static constexpr int CK = pick_ck();
+  static constexpr int NC = KS / CK;
+  static constexpr int CW = 16 * CK;                      // chunk columns
+  static constexpr int CB = KY * CW * 2;                  // bytes of one image part's chunk (16-bit)
+  static constexpr int SLOTB = 2 * NPART * CB;            // a chunk slot: [a, b] per part
   static constexpr int NSLOT0 = (232448 - FIXED) / SLOTB;
   static constexpr int NSLOT = NSLOT0 < 2 * NC ? NSLOT0 : 2 * NC;
   static constexpr int SMEM = FIXED + NSLOT * SLOTB;
