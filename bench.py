@@ -395,18 +395,19 @@ L2_NOTE = "flushed before each timed step (256 MiB write, untimed)"
 def _measure_fp32_peak(B, dev, stream, sm_count):
     """The FP32 multiply-add rate of this GPU, measured with the library's probe
     (fbf_debug_fp32_peak: 16 independent chains per thread, packed fma.rn.f32x2 pairs and
-    scalar fmaf), timed with CUDA events on the launching stream; best of five launches per
-    variant.  Returns a dict with TFLOP/s per variant and the peak (the larger)."""
+    scalar fmaf), timed with CUDA events on the launching stream; best of three launches of
+    about 4 ms (packed) per variant.  Returns a dict with TFLOP/s per variant and the peak
+    (the larger)."""
     import torch
     blocks, threads = 4 * sm_count, 256
     out = torch.empty(blocks * threads, dtype=torch.float32, device=dev)
     sh = stream.cuda_stream
     res = {}
+    iters = 1 << 15
     for name, pairs in (("ffma2", True), ("ffma", False)):
-        iters = 1 << 17
         B.fbf_debug_fp32_peak(pairs, blocks, threads, 1 << 10, out.data_ptr(), sh)   # warm-up
         best = 0.0
-        for _ in range(5):
+        for _ in range(3):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             flop = B.fbf_debug_fp32_peak(pairs, blocks, threads, iters, out.data_ptr(), sh)
@@ -415,7 +416,7 @@ def _measure_fp32_peak(B, dev, stream, sm_count):
             best = max(best, flop / (e0.elapsed_time(e1) / 1e3) / 1e12)
         res[name] = best
     res["peak"] = max(res["ffma2"], res["ffma"])
-    res["launch"] = f"{blocks} x {threads} threads, 16 chains x {1 << 17} multiply-adds per thread"
+    res["launch"] = f"{blocks} x {threads} threads, 16 chains x {iters} multiply-adds per thread"
     return res
 
 
