@@ -451,7 +451,7 @@ __device__ __forceinline__ void gen_chunk(unsigned char* dst, int c, const unsig
   constexpr int GSTEP = NCT / 8;                 // groups advanced per sweep
   const int r7 = ctid & 7;
   int rb = (ctid >> 3) / KG, cx = (ctid >> 3) % KG;
-#pragma unroll 2
+#pragma unroll 1
   for (int i = ctid; i < C::KY * KG; i += NCT) {
     const int hy = rb * 8 + r7;
     const int hx0 = (c * KG + cx) * 8;
