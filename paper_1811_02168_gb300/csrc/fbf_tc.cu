@@ -782,13 +782,20 @@ __device__ __forceinline__ void tc_body(const Src& src, const Scratch& sc) {
 #pragma unroll
             for (int e = 0; e < 8; e += 2) {
               const float x0 = __uint_as_float(v[jj][e]), x1 = __uint_as_float(v[jj][e + 1]);
-              v[jj][e] = to_tf32(x0);
-              v[jj][e + 1] = to_tf32(x1);
-              // the rounding error of hi, exact in FP32, as FP16 (used by the compensated form)
-              lo[e / 2] = pack2<__half>(x0 - __uint_as_float(v[jj][e]), x1 - __uint_as_float(v[jj][e + 1]));
+              if (NPART == 2) {
+                // compensated form: hi stays in place as the FP32 value, which the y pass
+                // reads as TF32 by dropping the low 13 mantissa bits; lo is what that drops
+                // (exact in FP32), as FP16
+                const float h0 = __uint_as_float(v[jj][e] & 0xFFFFE000u);
+                const float h1 = __uint_as_float(v[jj][e + 1] & 0xFFFFE000u);
+                lo[e / 2] = pack2<__half>(x0 - h0, x1 - h1);
+              } else {
+                v[jj][e] = to_tf32(x0);
+                v[jj][e + 1] = to_tf32(x1);
+              }
             }
-            tmem_st8(d1 + 8 * c, v[jj]);
             if (NPART == 2) tmem_st4(d1lo + 4 * c, lo);
+            else tmem_st8(d1 + 8 * c, v[jj]);
           }
         }
       }
