@@ -39,6 +39,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdint>
 #include <map>
 #include <mutex>
@@ -208,6 +209,20 @@ int kernel_slots(KernelFn fn, int nt, size_t smem, int dev, int* sms_out, int* o
 // Carried rows are used when the image has at least this many tiles per CTA.
 constexpr long long kCarryMinTilesPerCta = 3;
 
+// SM count of the current device (cached per device)
+int device_sms() {
+  static std::atomic<int> cache[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1 << 20;
+  int n = cache[dev].load(std::memory_order_relaxed);
+  if (n == 0) {
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) return 1 << 20;
+    cache[dev].store(n, std::memory_order_relaxed);
+  }
+  return n;
+}
+
 Work single_work(const float* in, float* out, int H, int W, size_t pitch, int K, int TY, int row0 = 0,
                  int rows = 0) {
   if (rows <= 0) rows = H - row0;
@@ -327,7 +342,14 @@ int launch_fp32(const DeviceParams& dp, const float* in, float* out, int H, int 
   if (r <= 9) return launch_cfg<9, 96, 512, 6>(dp, in, out, H, W, pitch, st, row0, rows);
   if (r <= 15) return launch_cfg<15, 96, 512, 6>(dp, in, out, H, W, pitch, st, row0, rows);
   if (r <= 24) return launch_cfg<24, 128, 256, 16>(dp, in, out, H, W, pitch, st, row0, rows);
-  if (r <= 30) return launch_cfg<30, 128, 256, 16>(dp, in, out, H, W, pitch, st, row0, rows);
+  if (r <= 30) {
+    // images with at least three 96-row tiles per SM carry their x-pass rows down the
+    // strips in a 96-row, 12-warp configuration; others take 128-row tiles with 8 warps
+    const long long tiles96 = (long long)((W + TX - 1) / TX) * (((rows > 0 ? rows : H - row0) + 95) / 96);
+    if (tiles96 >= kCarryMinTilesPerCta * device_sms())
+      return launch_cfg<30, 96, 384, 8>(dp, in, out, H, W, pitch, st, row0, rows);
+    return launch_cfg<30, 128, 256, 16>(dp, in, out, H, W, pitch, st, row0, rows);
+  }
   if (r <= 48) return launch_cfg<48, 64, 128, 16>(dp, in, out, H, W, pitch, st, row0, rows);
   return set_error(FBF_EUNSUPPORTED, "fbf_filter: radius too large");
 }

@@ -125,7 +125,11 @@ template <int RAD, int TY, int NT, int NY>
 struct Cfg {
   static constexpr int NW = NT / 32;                       // warps
   static constexpr int HROWS = TY + 2 * RAD;               // rows of the x-pass output
-  static constexpr int HROWS_P = (HROWS + 4 * NW - 1) / (4 * NW) * (4 * NW);  // whole rounds
+  // x-pass buffer rows: HROWS in whole 8-row groups (the k = 0 term convolves 8 rows per
+  // warp step; the last round of either term may leave warps idle); staged f rows: that, in
+  // whole rows per warp
+  static constexpr int XB = (HROWS + 7) / 8 * 8;
+  static constexpr int HROWS_P = (XB + NW - 1) / NW * NW;
   static constexpr int TXH = TX + 2 * RAD;                 // halo tile width
   static constexpr int FHS = TXH + 1;                      // f-halo row stride (floats)
   static constexpr int NQ2 = (NXH + 2 * RAD + 1) / 2;      // 16-byte loads per x-pass item
@@ -133,7 +137,7 @@ struct Cfg {
   static constexpr int SWP = SWP0 + ((2 - SWP0 % 16) + 16) % 16;   // == 2 (mod 16)
   static constexpr int STAGE_F2 = 8 * SWP;                 // per warp: 4 rows x 2 pairs
   static constexpr int HS2 = TX + 2;                       // x-pass buffer row stride (float2)
-  static constexpr int CPS0 = HROWS_P * HS2;
+  static constexpr int CPS0 = XB * HS2;
   static constexpr int CPS = CPS0 + ((4 - CPS0 % 16) + 16) % 16;  // pair stride, == 4 (mod 16)
   // f-halo staging: rows per warp, columns per lane, rows per group of loads in flight
   static constexpr int STAGE_RPW = HROWS_P / NW;
@@ -377,7 +381,7 @@ __device__ __forceinline__ void fbf_body(const Src& src, const Scratch& sc) {
   constexpr int CS1 = carry_rows(RAD, 4), CS0 = carry_rows(RAD, 8);
   constexpr int XR4 = (C::HROWS + 3) / 4 * 4, XR8 = (C::HROWS + 7) / 8 * 8;
   constexpr int CSLOT = 2 * CS1 * TX;
-  static_assert(XR8 <= C::HROWS_P && TY + CS1 <= C::HROWS, "carried rows must lie inside the buffer");
+  static_assert(XR8 == C::XB && XR8 <= C::HROWS_P && TY + CS1 <= C::HROWS, "carried rows must lie inside the buffer");
   constexpr int FS = TMA ? C::TMA_BW : C::FHS;        // f-halo row stride (floats)
   extern __shared__ float4 smem_f4[];
   // TMA: two f buffers first (128-byte aligned), then the plain path's layout without its f.
@@ -564,7 +568,7 @@ __device__ __forceinline__ void fbf_body(const Src& src, const Scratch& sc) {
       const int xr0 = carried ? cs : 0;
       if (k == 0) {
         // ---- term 0: pair (f - m, 1); eight halo rows per warp iteration -------------
-        for (int rb = xr0 + warp * 8; rb < (carried ? XR8 : C::HROWS_P); rb += C::NW * 8) {
+        for (int rb = xr0 + warp * 8; rb < XR8; rb += C::NW * 8) {
 #pragma unroll
           for (int r8 = 0; r8 < 8; ++r8) {
 #pragma unroll
@@ -581,7 +585,7 @@ __device__ __forceinline__ void fbf_body(const Src& src, const Scratch& sc) {
       } else {
         // ---- term k >= 1: pairs (C, S) and (f'C, f'S); four halo rows per iteration --
         const float2* tab = tabs + (k & 1) * TABN;
-        for (int rb = xr0 + warp * 4; rb < (carried ? XR4 : C::HROWS_P); rb += C::NW * 4) {
+        for (int rb = xr0 + warp * 4; rb < XR4; rb += C::NW * 4) {
           if (tile_int && interior) {
 #pragma unroll
             for (int r4 = 0; r4 < 4; ++r4) {
