@@ -203,13 +203,13 @@ def _fp32_kernel_name(plans, jobs, sm_count: int = 152) -> str:
     """The FP32 instantiation fbf_filter runs: f staged by TMA for radii <= 15 when the rows
     are 16-byte aligned (the bench's tensors are contiguous and freshly allocated); for radii
     above 15 the carried-row kernel when the image has at least three tiles per CTA (one CTA
-    per SM; tiles 32 wide, 128 rows high up to r = 30, else 64), else plain loads.  All are
+    per SM; tiles 32 wide, 96 rows high up to r = 30, else 64), else plain loads.  All are
     one source (fbf_fp32_body.cuh); DRAM traffic is recorded per family."""
     if all(p.radius <= 15 for p in plans) and all((j.W * 4) % 16 == 0 for j in jobs):
         return "fbf_fp32_tma_kernel"
 
     def tiles(p, j):
-        ty = 128 if p.radius <= 30 else 64
+        ty = 96 if p.radius <= 30 else 64
         return math.ceil(j.W / 32) * math.ceil(j.H / ty)
     if all(p.radius > 15 and tiles(p, j) >= 3 * sm_count for p, j in zip(plans, jobs)):
         return "fbf_fp32_carry_kernel"

@@ -149,9 +149,10 @@ const std::vector<RadClass>& classes() {
       {6, {cfg_entry<6, 112, 512, 7>("r6_ty112_nt512"), cfg_entry<6, 128, 256, 16>("r6_ty128_nt256")}},
       {9, {cfg_entry<9, 96, 512, 6>("r9_ty96_nt512")}},
       {15, {cfg_entry<15, 96, 512, 6>("r15_ty96_nt512"), cfg_entry<15, 128, 256, 16>("r15_ty128_nt256")}},
-      {24, {cfg_entry<24, 128, 256, 16, true>("r24_ty128_nt256_carry"), cfg_entry<24, 128, 256, 16>("r24_ty128_nt256")}},
-      {30, {cfg_entry<30, 128, 256, 16, true>("r30_ty128_nt256_carry"), cfg_entry<30, 128, 256, 16>("r30_ty128_nt256"),
-            cfg_entry<30, 96, 256, 12>("r30_ty96_nt256")}},
+      {24, {cfg_entry<24, 96, 384, 8, true>("r24_ty96_nt384_carry"), cfg_entry<24, 128, 256, 16, true>("r24_ty128_nt256_carry"),
+            cfg_entry<24, 128, 256, 16>("r24_ty128_nt256")}},
+      {30, {cfg_entry<30, 96, 384, 8, true>("r30_ty96_nt384_carry"), cfg_entry<30, 128, 256, 16, true>("r30_ty128_nt256_carry"),
+            cfg_entry<30, 128, 256, 16>("r30_ty128_nt256"), cfg_entry<30, 96, 256, 12>("r30_ty96_nt256")}},
       {48, {cfg_entry<48, 64, 128, 16, true>("r48_ty64_nt128_carry"), cfg_entry<48, 64, 128, 16>("r48_ty64_nt128")}},
       {6, {tc_entry<6, FBF_FP16_TC>("tc_fp16_r6")}, FBF_FP16_TC},
       {15, {tc_entry<15, FBF_FP16_TC>("tc_fp16_r15")}, FBF_FP16_TC},

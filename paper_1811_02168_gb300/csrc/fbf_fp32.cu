@@ -341,13 +341,16 @@ int launch_fp32(const DeviceParams& dp, const float* in, float* out, int H, int 
   if (r <= 6) return launch_cfg<6, 112, 512, 7>(dp, in, out, H, W, pitch, st, row0, rows);
   if (r <= 9) return launch_cfg<9, 96, 512, 6>(dp, in, out, H, W, pitch, st, row0, rows);
   if (r <= 15) return launch_cfg<15, 96, 512, 6>(dp, in, out, H, W, pitch, st, row0, rows);
-  if (r <= 24) return launch_cfg<24, 128, 256, 16>(dp, in, out, H, W, pitch, st, row0, rows);
+  // 15 < r <= 30: images with at least three 96-row tiles per SM carry their x-pass rows
+  // down the strips in a 96-row, 12-warp configuration; others take 128-row tiles, 8 warps
+  const long long tiles96 = (long long)((W + TX - 1) / TX) * (((rows > 0 ? rows : H - row0) + 95) / 96);
+  const bool carry96 = tiles96 >= kCarryMinTilesPerCta * device_sms();
+  if (r <= 24) {
+    if (carry96) return launch_cfg<24, 96, 384, 8>(dp, in, out, H, W, pitch, st, row0, rows);
+    return launch_cfg<24, 128, 256, 16>(dp, in, out, H, W, pitch, st, row0, rows);
+  }
   if (r <= 30) {
-    // images with at least three 96-row tiles per SM carry their x-pass rows down the
-    // strips in a 96-row, 12-warp configuration; others take 128-row tiles with 8 warps
-    const long long tiles96 = (long long)((W + TX - 1) / TX) * (((rows > 0 ? rows : H - row0) + 95) / 96);
-    if (tiles96 >= kCarryMinTilesPerCta * device_sms())
-      return launch_cfg<30, 96, 384, 8>(dp, in, out, H, W, pitch, st, row0, rows);
+    if (carry96) return launch_cfg<30, 96, 384, 8>(dp, in, out, H, W, pitch, st, row0, rows);
     return launch_cfg<30, 128, 256, 16>(dp, in, out, H, W, pitch, st, row0, rows);
   }
   if (r <= 48) return launch_cfg<48, 64, 128, 16>(dp, in, out, H, W, pitch, st, row0, rows);
