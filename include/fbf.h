@@ -360,6 +360,14 @@ int fbf_server_reset_stats(fbf_server_t s);
  * (NULL ok). */
 int fbf_server_destroy(fbf_server_t s);
 
+/* fbf_debug_server_inject -- test aid, not part of the method: the server's next `count`
+ * uploads (stage 1) or batched launches (stage 2) fail on the host with FBF_ECUDA before
+ * any CUDA work of that step (a launch fails with its requests' images already queued in
+ * the server's batch), so that a test drives the loop's failure handling -- the failed
+ * requests end with the error, their buffers and budget are released, later requests are
+ * served -- without a device fault.  count 0 clears.  FBF_EINVAL for a bad stage or count. */
+int fbf_debug_server_inject(fbf_server_t s, int stage, int count);
+
 /* fbf_last_error -- message for the last failing call on this thread ("" if none). */
 /*
  * fbf_brute_filter -- eq. (1) evaluated directly with the Gaussian range kernel of eq. (2)

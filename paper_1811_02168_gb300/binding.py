@@ -114,6 +114,7 @@ SIGNATURES = {
     "fbf_last_error": (ctypes.c_char_p, []),
     "fbf_version": (ctypes.c_char_p, []),
     "fbf_debug_set_wait_limit": (ctypes.c_int, [ctypes.c_int]),
+    "fbf_debug_server_inject": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     "fbf_debug_fp32_peak": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_longlong,
                                            ctypes.c_void_p, ctypes.c_void_p, _c_double_p]),
     "fbf_debug_error_curve": (ctypes.c_int, [_c_double_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -380,6 +381,11 @@ def fbf_last_error() -> str:
 
 def fbf_version() -> str:
     return lib().fbf_version().decode()
+
+
+def fbf_debug_server_inject(server: int, stage: int, count: int) -> None:
+    """Test aid: the server's next `count` uploads (stage 1) or launches (stage 2) fail."""
+    _check(lib().fbf_debug_server_inject(server, stage, count), "fbf_debug_server_inject")
 
 
 def fbf_debug_set_wait_limit(polls: int) -> None:

@@ -22,6 +22,7 @@
 
 #include <algorithm>
 #include <array>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
@@ -100,9 +101,19 @@ struct fbf_server_s {
   double t_first = -1, t_last = -1;
   std::vector<std::array<double, 6>> trace;   // latency, queued, wait, launch->result, px, batch
   std::thread worker;
+  // test hook (fbf_debug_server_inject): uploads / launches still to fail on the host
+  std::atomic<int> inject_upload{0}, inject_launch{0};
 };
 
 namespace {
+
+// one injected failure of a stage, if any is left (test hook)
+bool take_injected(std::atomic<int>& n) {
+  int v = n.load();
+  while (v > 0)
+    if (n.compare_exchange_weak(v, v - 1)) return true;
+  return false;
+}
 
 // After a failed upload or launch: wait (best effort) for the copies and kernels that may
 // still use a request's buffers, then give the buffers back to the pool (called without
@@ -124,6 +135,11 @@ void release_after_error(fbf_server_s* s, const std::vector<Req*>& reqs) {
 // Device buffers and the upload of one admitted request (called without the lock).
 int upload(fbf_server_s* s, Req* r) {
   const fbf::NvtxRange tr("fbf_server admit: upload");
+  if (take_injected(s->inject_upload)) {
+    const int rc = fbf::set_error(FBF_ECUDA, "fbf_server: upload: injected failure");
+    release_after_error(s, {r});
+    return rc;
+  }
   const size_t n = (size_t)r->H * r->W * sizeof(float);
   void* a = nullptr;
   void* b = nullptr;
@@ -153,6 +169,8 @@ int launch(fbf_server_s* s, Launch& L) {
     const int rc = fbf_batch_submit(s->batch, r->plan, r->d_in, r->d_out, r->H, r->W, (size_t)r->W, nullptr);
     if (rc != FBF_OK) return rc;
   }
+  // test hook: fail with the images queued in the batch, as a failing submit would leave them
+  if (take_injected(s->inject_launch)) return fbf::set_error(FBF_ECUDA, "fbf_server: launch: injected failure");
   int rc = fbf_launch(s->batch, s->comp);
   if (rc != FBF_OK) return rc;
   cudaEvent_t kd = nullptr;
@@ -532,5 +550,12 @@ int fbf_server_destroy(fbf_server_t s) try {
   delete s;
   return FBF_OK;
 } FBF_ABI_CATCH("fbf_server_destroy")
+
+int fbf_debug_server_inject(fbf_server_t s, int stage, int count) try {
+  if (!s || count < 0 || (stage != 1 && stage != 2))
+    return fbf::set_error(FBF_EINVAL, "fbf_debug_server_inject: bad arguments");
+  (stage == 1 ? s->inject_upload : s->inject_launch).store(count);
+  return FBF_OK;
+} FBF_ABI_CATCH("fbf_debug_server_inject")
 
 }  // extern "C"

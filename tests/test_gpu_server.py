@@ -136,3 +136,36 @@ def test_served_in_a_mix_matches_the_oracle(B, form, tol):
         scale = max(1.0, float(np.abs(ref).max()) / 255.0)
         err = float(np.abs(hout[i].numpy() - ref).max())
         assert err <= tol * scale, (i, r["H"], r["W"], r["theta"], r["sigma"], r["K"], err)
+
+
+def test_injected_failures_fail_only_their_requests(B):
+    """Failure handling of the native loop, driven on the host (fbf_debug_server_inject: no
+    device fault): with a budget of exactly two images, three failing uploads and then a
+    failing batched launch end only their own requests with FBF_ECUDA; their buffers and
+    budget come back (otherwise later requests could never be admitted and the drain would
+    time out), the batch left with queued images is made anew, and every other request is
+    served with fbf_filter's result."""
+    n, H, W = 14, 256, 256
+    imgs = [voronoi_image(H, W, 10, 30.0, 10.0, seed=3000 + i) for i in range(n)]
+    hin = [torch.from_numpy(im).pin_memory() for im in imgs]
+    hout = [torch.full((H, W), -1.0).pin_memory() for _ in range(n)]
+    srv = B.Server(precision=B.FBF_FP32, hbm_budget_bytes=2 * 8 * H * W, max_batch=4, max_inflight=2)
+    B.fbf_debug_server_inject(srv.handle, 1, 3)
+    first = srv.replay([0.0] * 7, hin[:7], hout[:7], [3.0] * 7, [30.0] * 7, [4] * 7)
+    srv.drain(60.0)
+    st1 = [srv.poll(t) for t in first]
+    assert st1.count(B.FBF_ECUDA) == 3 and st1.count(B.FBF_DONE) == 4, st1
+    B.fbf_debug_server_inject(srv.handle, 2, 1)
+    second = srv.replay([0.0] * 7, hin[7:], hout[7:], [3.0] * 7, [30.0] * 7, [4] * 7)
+    srv.drain(60.0)
+    st2 = [srv.poll(t) for t in second]
+    stats = srv.stats()
+    srv.close()
+    failed2 = st2.count(B.FBF_ECUDA)
+    assert 1 <= failed2 <= 4 and st2.count(B.FBF_DONE) == 7 - failed2, st2
+    assert stats["failed"] == 3 + failed2 and stats["requests"] == n - 3 - failed2
+    plans = {}
+    for i, s in enumerate(st1 + st2):
+        if s == B.FBF_DONE:
+            r = dict(theta=3.0, sigma=30.0, K=4, H=H, W=W, img=imgs[i])
+            assert _close(hout[i], _alone(B, plans, r, B.FBF_FP32)), i
