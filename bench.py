@@ -807,7 +807,7 @@ def run_psnr(a):
 
 def run_batch(a):
     """64 images (sides log-uniform in [256, 2048], theta in {2,5,10}, sigma in {10,30,80},
-    K from eps 0.01) in one batched launch per radius class, captured once as a CUDA graph;
+    K from eps 0.01) in one batched launch per radius class and theta, captured once as a CUDA graph;
     one step = one graph replay (work-list upload + kernels).  Single GPU."""
     import numpy as np
     import torch
@@ -894,12 +894,12 @@ def run_batch(a):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "batch_64_images_256_to_2048", "images": len(jobs), "pixels": px,
                    "radius_classes": classes, "plans": len(plans),
-                   "launch": "one CUDA graph replay: work-list upload + one persistent kernel per radius class",
+                   "launch": "one CUDA graph replay: work-list upload + one persistent kernel per radius class and theta",
                    "one_at_a_time_ms": sum(one) / len(one),
                    "l2": "flushed before each timed step (256 MiB write, untimed)"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None,
-                     "kernel": "fbf_fp32_batch_kernel / fbf_fp32_batch_carry_kernel (per radius class)",
+                     "kernel": "fbf_fp32_batch_kernel / fbf_fp32_batch_carry_kernel (per radius class and theta)",
                      "peak_source": "measured on this GPU by the FP32 multiply-add probe (fbf_debug_fp32_peak, "
                                     f"{probe['launch']}): {probe['ffma2']:.2f} TFLOP/s packed",
                      "frac_of_derived_peak": achieved / derived, "derived_peak_source": derived_src,

@@ -200,8 +200,8 @@ typedef uint64_t fbf_ticket_t;
 /*
  * fbf_batch_create -- a batch context.  Images are queued with fbf_batch_submit and filtered
  * together by fbf_launch: per precision form and radius class (the kernel instantiation
- * serving their r = ceil(3 theta)) one persistent stream-K launch runs over a device
- * work-list of all
+ * serving their r = ceil(3 theta)), and for FBF_FP32 per spatial kernel (theta) within the
+ * class, one persistent stream-K launch runs over a device work-list of all
  * (image, tile, cosine term) units, so small and large images share the GPU evenly.  Not
  * in the paper (Section III filters one image at a time); the arithmetic per image is
  * exactly fbf_filter's.  max_images (>= 1) bounds one launch; flags: FBF_BATCH_AUTOTUNE,

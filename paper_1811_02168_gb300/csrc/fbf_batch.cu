@@ -1,10 +1,12 @@
 // Batched Fourier bilateral filtering: many images in one persistent launch.
 //
 // Images are queued with fbf_batch_submit (host only), then fbf_launch groups them by radius
-// class (the kernel instantiation that serves their r = ceil(3 theta)), uploads one device
-// work-list per class (per-image Work records and per-plan DeviceParams, one copy from a
-// pinned staging buffer) and starts one stream-K persistent kernel per class over the
-// concatenated (image, tile, term) sequence of the class.  An event recorded after the
+// class (the kernel instantiation that serves their r = ceil(3 theta)) and, for the FP32
+// form, by spatial kernel within the class (the launch's taps are a kernel parameter, read
+// from the constant bank by the multiply-adds), uploads one device work-list per group
+// (per-image Work records and per-plan DeviceParams, one copy from a pinned staging buffer)
+// and starts one stream-K persistent kernel per group over the concatenated (image, tile,
+// term) sequence of the group.  An event recorded after the
 // launches marks the generation; tickets name a generation and fbf_batch_poll / fbf_batch_wait query
 // it.  fbf_batch_capture records the same work as a CUDA graph (copy + kernels) that
 // fbf_batch_replay relaunches with the same pointers and sizes.
@@ -39,9 +41,10 @@ using namespace fp32;
 struct ClassLaunch {
   // launches the batched kernel of one configuration; returns FBF_OK or an error code.
   // carry / kmax: the carried-row slots (configurations with carry_bytes_per_term) and the
-  // largest K of the work-list
+  // largest K of the work-list; taps: the spatial taps every image of the list shares (FP32)
   int (*launch)(const DeviceParams* dparams, const Work* dwork, int n, long long wtot,
-                float* partial, int* counter, float2* carry, int kmax, cudaStream_t st, int dev);
+                float* partial, int* counter, float2* carry, int kmax, const SpatialTaps& taps,
+                cudaStream_t st, int dev);
   // partial-sum bytes one launch of this configuration needs (per CTA slots) on dev
   int (*partial_bytes)(int dev, size_t* out);
   // carried-row bytes per cosine term of the longest image (0: rows are not carried)
@@ -96,7 +99,8 @@ struct BatchCfg {
     return FBF_OK;
   }
   static int launch(const DeviceParams* dparams, const Work* dwork, int n, long long wtot,
-                    float* partial, int* counter, float2* carry, int kmax, cudaStream_t st, int dev) {
+                    float* partial, int* counter, float2* carry, int kmax, const SpatialTaps& taps,
+                    cudaStream_t st, int dev) {
     int G = 0;
     int rc = slots(dev, &G);
     if (rc != FBF_OK) return rc;
@@ -108,7 +112,7 @@ struct BatchCfg {
     sc.counter = counter;
     sc.carry = carry;
     sc.kmax = kmax;
-    kernel()<<<(unsigned)g, NT, C::SMEM_BYTES, st>>>(dparams, dwork, n, sc);
+    kernel()<<<(unsigned)g, NT, C::SMEM_BYTES, st>>>(dparams, dwork, n, sc, taps);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return set_error(FBF_ECUDA, std::string("fbf_batch: ") + cudaGetErrorString(e));
     return FBF_OK;
@@ -133,7 +137,7 @@ struct RadClass {
 // tensor-core forms: one configuration per (radius class, precision), 128 x 64 tiles
 template <int RAD, int PREC>
 int tc_launch(const DeviceParams* dparams, const Work* dwork, int n, long long wtot, float* partial, int* counter,
-              float2*, int, cudaStream_t st, int dev) {
+              float2*, int, const SpatialTaps&, cudaStream_t st, int dev) {
   return launch_tc_batch(RAD, PREC, dparams, dwork, n, wtot, partial, counter, st, dev);
 }
 template <int RAD, int PREC>
@@ -289,9 +293,12 @@ int ensure_device(Batch* b) {
   return FBF_OK;
 }
 
+// One launch: the images of one radius class (FP32: and one spatial kernel, whose taps the
+// kernel takes from its parameters)
 struct ClassPlan {
   int cls = -1;
   int cand = 0;
+  SpatialTaps taps{};
   std::vector<Work> works;
   std::vector<DeviceParams> params;
   long long wtot = 0, tiles = 0, pixels = 0;
@@ -301,14 +308,32 @@ struct ClassPlan {
 
 // group the pending images by radius class and lay out the device lists
 int build_lists(Batch* b, std::vector<ClassPlan>* out, size_t* bytes) {
-  std::map<int, ClassPlan> by;
+  // FP32 classes: one launch per distinct spatial kernel (padded taps) within the class, in
+  // order of first appearance; tensor-core classes stage each image's taps themselves
+  std::map<std::pair<int, int>, ClassPlan> by;
+  std::map<int, std::vector<SpatialTaps>> tapsets;
   for (const Pending& pd : b->pending) {
     const int cls = class_of(pd.r, pd.precision);
     if (cls < 0) return set_error(FBF_EUNSUPPORTED, "fbf_batch: radius too large");
-    ClassPlan& cp = by[cls];
+    const int rad = classes()[cls].rad;
+    const DeviceParams q = padded(pd.dp, rad);
+    SpatialTaps tq{};
+    for (int i = 0; i <= 2 * rad; ++i) tq.g[i] = q.g[i];
+    int ts = 0;
+    if (classes()[cls].precision == FBF_FP32) {
+      std::vector<SpatialTaps>& seen = tapsets[cls];
+      ts = -1;
+      for (size_t i = 0; i < seen.size() && ts < 0; ++i)
+        if (std::memcmp(seen[i].g, tq.g, sizeof(tq.g)) == 0) ts = (int)i;
+      if (ts < 0) {
+        seen.push_back(tq);
+        ts = (int)seen.size() - 1;
+      }
+    }
+    ClassPlan& cp = by[{cls, ts}];
     cp.cls = cls;
-    // one DeviceParams per distinct plan in the class
-    const DeviceParams q = padded(pd.dp, classes()[cls].rad);
+    cp.taps = tq;
+    // one DeviceParams per distinct plan in the launch
     int pidx = -1;
     for (size_t i = 0; i < cp.params.size() && pidx < 0; ++i)
       if (std::memcmp(&q, &cp.params[i], sizeof(DeviceParams)) == 0) pidx = (int)i;
@@ -489,7 +514,7 @@ int launch_classes(Batch* b, const std::vector<ClassPlan>& cps, size_t list_byte
                                  : nullptr;
     rc = cl.launch(reinterpret_cast<const DeviceParams*>(d + cp.params_off),
                    reinterpret_cast<const Work*>(d + cp.work_off), (int)cp.works.size(), cp.wtot,
-                   scratch_partials(b), scratch_counters(b), carry, cp.kmax, st, b->dev);
+                   scratch_partials(b), scratch_counters(b), carry, cp.kmax, cp.taps, st, b->dev);
     if (rc != FBF_OK) return rc;
   }
   return FBF_OK;

@@ -184,6 +184,13 @@ struct Scratch {
   int kmax;                           // largest K of the launch's images (carry slots per CTA)
 };
 
+// The spatial taps of a batched launch, in the constant bank (kernel parameter): all images
+// of one launch share their Gaussian, so the multiply-adds of both passes take their taps
+// from the constant bank as the single-image kernels do, not from per-image loads.
+struct SpatialTaps {
+  float g[2 * FBF_MAX_RADIUS + 1];
+};
+
 // A single image whose parameters sit in the constant bank (kernel parameter).
 struct SingleSrc {
   static constexpr bool kTma = false;
@@ -193,6 +200,7 @@ struct SingleSrc {
   __device__ __forceinline__ int count() const { return 1; }
   __device__ __forceinline__ Work work(int) const { return w; }
   __device__ __forceinline__ const DeviceParams& params(int) const { return *p; }
+  __device__ __forceinline__ const DeviceParams& taps(const DeviceParams& q) const { return q; }
   __device__ __forceinline__ int find(long long) const { return 0; }
 };
 
@@ -208,6 +216,7 @@ struct SingleSrcTma {
   __device__ __forceinline__ int count() const { return 1; }
   __device__ __forceinline__ Work work(int) const { return w; }
   __device__ __forceinline__ const DeviceParams& params(int) const { return *p; }
+  __device__ __forceinline__ const DeviceParams& taps(const DeviceParams& q) const { return q; }
   __device__ __forceinline__ int find(long long) const { return 0; }
 };
 
@@ -227,6 +236,7 @@ struct SingleSrcCarry {
   __device__ __forceinline__ int count() const { return 1; }
   __device__ __forceinline__ Work work(int) const { return w; }
   __device__ __forceinline__ const DeviceParams& params(int) const { return *p; }
+  __device__ __forceinline__ const DeviceParams& taps(const DeviceParams& q) const { return q; }
   __device__ __forceinline__ int find(long long) const { return 0; }
 };
 
@@ -243,9 +253,11 @@ struct ListSrcT {
   const DeviceParams* __restrict__ prm;
   const Work* __restrict__ wl;
   int n;
+  const SpatialTaps* tp;   // the launch's taps (every image of the list has them)
   __device__ __forceinline__ int count() const { return n; }
   __device__ __forceinline__ Work work(int i) const { return wl[i]; }
   __device__ __forceinline__ const DeviceParams& params(int i) const { return prm[wl[i].param_idx]; }
+  __device__ __forceinline__ const SpatialTaps& taps(const DeviceParams&) const { return *tp; }
   // last image whose weighted start is <= s
   __device__ __forceinline__ int find(long long s) const {
     int lo = 0, hi = n - 1;
@@ -336,15 +348,15 @@ __device__ __forceinline__ float2 tab_lookup(const float2* tab2, float v) {
 }
 
 // tap d of 0..2*RAD, read through the symmetric half so only RAD+1 registers are live
-template <int RAD>
-__device__ __forceinline__ float2 tap2(const DeviceParams& p, int d) {
+template <int RAD, class TP>
+__device__ __forceinline__ float2 tap2(const TP& p, int d) {
   const float g = p.g[d <= RAD ? d : 2 * RAD - d];
   return make_float2(g, g);
 }
 
 // x pass of one item: 8 consecutive outputs of one float2 image pair in one row.
-template <int RAD>
-__device__ __forceinline__ void xconv8(const float2* __restrict__ srow, const DeviceParams& p,
+template <int RAD, class TP>
+__device__ __forceinline__ void xconv8(const float2* __restrict__ srow, const TP& p,
                                        float2* __restrict__ dst) {
   constexpr int NQ2 = (NXH + 2 * RAD + 1) / 2;
   float2 acc[NXH];
@@ -444,6 +456,7 @@ __device__ __forceinline__ void fbf_body(const Src& src, const Scratch& sc) {
   while (img < img_end || (img == img_end && u < u_end)) {
     const Work wk = src.work(img);
     const DeviceParams& p = src.params(img);
+    const auto& pt = src.taps(p);   // the taps, in the constant bank
     const int K = wk.K;
     const int H = wk.H, W = wk.W;
     const long long pitch = wk.pitch;
@@ -578,7 +591,7 @@ __device__ __forceinline__ void fbf_body(const Src& src, const Scratch& sc) {
             }
           }
           __syncwarp();
-          xconv8<RAD>(stage + x_row8 * C::SWP + x_xg * NXH, p,
+          xconv8<RAD>(stage + x_row8 * C::SWP + x_xg * NXH, pt,
                       hbuf + (rb + x_row8) * C::HS2 + x_xg * NXH);
           __syncwarp();
         }
@@ -630,7 +643,7 @@ __device__ __forceinline__ void fbf_body(const Src& src, const Scratch& sc) {
             }
           }
           __syncwarp();
-          xconv8<RAD>(stage + (x_row4 * 2 + x_cp) * C::SWP + x_xg * NXH, p,
+          xconv8<RAD>(stage + (x_row4 * 2 + x_cp) * C::SWP + x_xg * NXH, pt,
                       hbuf + x_cp * C::CPS + (rb + x_row4) * C::HS2 + x_xg * NXH);
           __syncwarp();
         }
@@ -684,7 +697,7 @@ __device__ __forceinline__ void fbf_body(const Src& src, const Scratch& sc) {
 #pragma unroll
           for (int a = 0; a < NY; ++a) {
             const int d = q - a;
-            if (d >= 0 && d <= 2 * RAD) acc[a] = __ffma2_rn(tap2<RAD>(p, d), v, acc[a]);
+            if (d >= 0 && d <= 2 * RAD) acc[a] = __ffma2_rn(tap2<RAD>(pt, d), v, acc[a]);
           }
         }
         if (k == 0) {
@@ -796,22 +809,24 @@ fbf_fp32_carry_kernel(const __grid_constant__ DeviceParams p, const Work w, cons
   fbf_body<RAD, TY, NT, NY>(src, sc);
 }
 
-// A device work-list of images sharing one radius class (batched launch).
+// A device work-list of images sharing one radius class and one spatial kernel (batched
+// launch).
 template <int RAD, int TY, int NT, int NY>
 __global__ void __launch_bounds__(NT, 1)
 fbf_fp32_batch_kernel(const DeviceParams* __restrict__ params, const Work* __restrict__ work,
-                      int n, const Scratch sc) {
-  const ListSrc src{params, work, n};
+                      int n, const Scratch sc, const __grid_constant__ SpatialTaps taps) {
+  const ListSrc src{params, work, n, &taps};
   fbf_body<RAD, TY, NT, NY>(src, sc);
 }
 
 
-// A device work-list of images sharing one radius class, x-pass rows carried down each strip.
+// A device work-list of images sharing one radius class and one spatial kernel, x-pass rows
+// carried down each strip.
 template <int RAD, int TY, int NT, int NY>
 __global__ void __launch_bounds__(NT, 1)
 fbf_fp32_batch_carry_kernel(const DeviceParams* __restrict__ params, const Work* __restrict__ work,
-                            int n, const Scratch sc) {
-  const ListSrcT<true> src{params, work, n};
+                            int n, const Scratch sc, const __grid_constant__ SpatialTaps taps) {
+  const ListSrcT<true> src{params, work, n, &taps};
   fbf_body<RAD, TY, NT, NY>(src, sc);
 }
 

@@ -993,7 +993,7 @@ fbf_tc_kernel(const __grid_constant__ DeviceParams p, const Work w, const Scratc
 template <int RAD, typename T>
 __global__ void __launch_bounds__(NTHREADS, 1)
 fbf_tc_batch_kernel(const DeviceParams* __restrict__ prm, const Work* __restrict__ wl, int n, const Scratch sc) {
-  const ListSrc src{prm, wl, n};
+  const ListSrc src{prm, wl, n, nullptr};   // taps come from prm (staged per image)
   tc_body<RAD, T>(src, sc);
 }
 

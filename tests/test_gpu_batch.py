@@ -376,3 +376,33 @@ def test_batch_carries_rows_for_wide_radii(B):
     ref = ofl.fourier_bf(x.cpu().numpy().astype(np.float64), plan.theta, op.c, op.T)
     assert np.abs(y.cpu().numpy() - ref).max() <= TOL
     batch.close()
+
+
+def test_batch_mixes_spatial_kernels_within_a_radius_class(B):
+    """FP32 batches launch each radius class once per spatial kernel (the launch's taps are a
+    kernel parameter): images of one class with different theta -- r = 4, 5, 6 in the r <= 6
+    class, 11, 12, 15 in the r <= 15 class, 27, 30 in the r <= 30 class (rows carried down
+    the strips) -- submitted interleaved in one batch each match the oracle with their own
+    theta, also after a graph replay."""
+    specs = [(90, 70, 1.3, 30.0, 5), (130, 210, 3.5, 10.0, 8), (330, 90, 9.0, 30.0, 4),
+             (75, 160, 1.6, 80.0, 3), (140, 100, 5.0, 30.0, 5), (300, 130, 10.0, 80.0, 6),
+             (64, 64, 2.0, 10.0, 8), (110, 150, 4.0, 80.0, 4)]
+    assert sorted(int(np.ceil(3 * t)) for _, _, t, _, _ in specs) == [4, 5, 6, 11, 12, 15, 27, 30]
+    batch = B.Batch(16)
+    items = []
+    for i, (H, W, theta, sigma, K) in enumerate(specs):
+        img = voronoi_image(H, W, 12, 30.0, 10.0, seed=900 + i)
+        plan = B.Plan(sigma, 255, theta, K=K)
+        x = torch.from_numpy(img).cuda()
+        y = torch.full_like(x, -1.0)
+        batch.submit(plan, x, y)
+        items.append((img, plan, x, y, theta, sigma, K))
+    stream = torch.cuda.current_stream()
+    batch.capture(stream)
+    batch.replay(stream)
+    torch.cuda.synchronize()
+    for img, plan, x, y, theta, sigma, K in items:
+        op = ofit.make_plan(sigma, 255, K=K)
+        ref = ofl.fourier_bf(img.astype(np.float64), theta, op.c, op.T)
+        assert np.abs(y.cpu().numpy() - ref).max() <= TOL, (theta, sigma, K)
+    batch.close()
