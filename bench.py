@@ -936,7 +936,8 @@ def run_serve(a):
       * open loop at --serve-rate for --serve-seconds: p50/p99 latency (submit to result on
         the host) and served Mpix/s;
       * capacity: a backlog of requests all arriving at once, sustained Mpix/s = pixels /
-        makespan;
+        makespan (after an untimed pass of the same backlog on the same server, so that the
+        memory pool already holds what the run's high water needs);
       * rate sweep (first two modes): open loop at fractions of the measured capacity for a
         few seconds each, p50/p99 per offered rate, and the knee (the highest offered rate
         served at >= 90% with p99 within 4x of the lightest load's);
@@ -991,20 +992,22 @@ def run_serve(a):
 
     warm = make_requests(backlog_jobs[:256], t_scale=0.0)
 
-    def serve(prec, batching, reqs, check=()):
+    def serve(prec, batching, reqs, check=(), warm_reqs=None):
         """The library's serving loop: warm-up on the same server -- every parameter set once
-        (plans, kernels), then a burst of 256 requests of the workload's sizes at once (the
-        memory pool, the batch's work-list and split-tile buffers grown to the sizes the run
-        needs) -- statistics cleared, then the requests replayed at their arrival times.
-        Requests listed in `check` get their own result buffers."""
+        (plans, kernels), then `warm_reqs` at once (default: a burst of 256 requests of the
+        workload's sizes; the capacity run passes its whole backlog): the memory pool, the
+        batch's work-list and split-tile buffers grown to the sizes the run needs --
+        statistics cleared, then the requests replayed at their arrival times.  Requests
+        listed in `check` get their own result buffers."""
+        wr = warm if warm_reqs is None else warm_reqs
         srv = B.Server(precision=prec, hbm_budget_bytes=40 << 30, max_batch=256 if batching else 1,
                        max_inflight=2)
         for i, (th, sg, K) in enumerate(warm_params):
             x = cls_img[small_cls]
             srv.submit(x, ring[:x.numel()].view(x.shape), th, sg, K=K)
         srv.drain(600.0)
-        srv.replay([0.0] * len(warm), [r.host_in for r in warm], [r.host_out for r in warm],
-                   [r.theta for r in warm], [r.sigma for r in warm], [r.K for r in warm])
+        srv.replay([0.0] * len(wr), [r.host_in for r in wr], [r.host_out for r in wr],
+                   [r.theta for r in wr], [r.sigma for r in wr], [r.K for r in wr])
         srv.drain(600.0)
         srv.reset_stats()
         outs = {i: torch.empty(reqs[i].host_in.shape, dtype=torch.float32).pin_memory() for i in check}
@@ -1056,7 +1059,7 @@ def run_serve(a):
                 reqs, idle_sleep=a.serve_idle_sleep)
             res["open_loop"] = st.summary()
         bl = make_requests(backlog_jobs, t_scale=0.0)
-        res["capacity"], _ = serve(prec, batching, bl)
+        res["capacity"], _ = serve(prec, batching, bl, warm_reqs=bl)
         results[mode] = res
     # rate sweep around each main mode's capacity
     mean_px = statistics.mean(r.H * r.W for r in make_requests(backlog_jobs))
