@@ -200,19 +200,20 @@ def _traffic_for(kernel: str):
 
 
 def _fp32_kernel_name(plans, jobs, sm_count: int = 152) -> str:
-    """The FP32 instantiation fbf_filter runs: f staged by TMA for radii <= 15 when the rows
-    are 16-byte aligned (the bench's tensors are contiguous and freshly allocated); for radii
-    above 15 the carried-row kernel when the image has at least three tiles per CTA (one CTA
-    per SM; tiles 32 wide, 96 rows high up to r = 30, else 64), else plain loads.  All are
-    one source (fbf_fp32_body.cuh); DRAM traffic is recorded per family."""
+    """The FP32 instantiation fbf_filter runs: for r > 15 the carried-row kernel when the
+    image has at least three tiles per CTA (one CTA per SM; tiles 32 wide, 96 rows high up to
+    r = 30, else 64), for radii <= 15 f staged by TMA when the rows are 16-byte aligned (the
+    bench's tensors are contiguous and freshly allocated), else plain loads.  All are one
+    source (fbf_fp32_body.cuh); DRAM traffic is recorded per family."""
+    def carried(p, j):
+        if p.radius <= 15:
+            return False
+        ty = 96 if p.radius <= 30 else 64
+        return math.ceil(j.W / 32) * math.ceil(j.H / ty) >= 3 * sm_count
+    if all(carried(p, j) for p, j in zip(plans, jobs)):
+        return "fbf_fp32_carry_kernel"
     if all(p.radius <= 15 for p in plans) and all((j.W * 4) % 16 == 0 for j in jobs):
         return "fbf_fp32_tma_kernel"
-
-    def tiles(p, j):
-        ty = 96 if p.radius <= 30 else 64
-        return math.ceil(j.W / 32) * math.ceil(j.H / ty)
-    if all(p.radius > 15 and tiles(p, j) >= 3 * sm_count for p, j in zip(plans, jobs)):
-        return "fbf_fp32_carry_kernel"
     return "fbf_fp32_kernel"
 
 

@@ -346,6 +346,7 @@ int build_lists(Batch* b, std::vector<ClassPlan>* out, size_t* bytes) {
     w.out = pd.out;
     w.pitch = (long long)pd.pitch;
     w.H = pd.H;
+    w.row1 = pd.H;
     w.W = pd.W;
     w.K = pd.dp.K;
     w.wtile = 2 * w.K - 1;

@@ -228,6 +228,7 @@ Work single_work(const float* in, float* out, int H, int W, size_t pitch, int K,
   if (rows <= 0) rows = H - row0;
   Work w{};
   w.row0 = row0;
+  w.row1 = row0 + rows;
   w.in = in;
   w.out = out;
   w.pitch = (long long)pitch;
@@ -258,8 +259,18 @@ int launch_cfg(const DeviceParams& dp, const float* in, float* out, int H, int W
   int rc = FBF_OK;
   CUtensorMap map;
   bool tma = false;
+  // Carried x-pass rows pay when each CTA's range covers several tiles of a strip (the
+  // first tile of a range convolves all its rows) and carrying saves a whole x-pass round
+  // per tile; carried tiles stage f with plain loads (the TMA staging is not combined)
+  constexpr int CSLOT = 2 * carry_rows(RAD, 4) * TX;
+  constexpr bool kCarryCfg = carry_saves_round(RAD, TY, NT);
+  bool want_carry = false;
+  if constexpr (kCarryCfg) {
+    const long long tiles = (long long)((W + TX - 1) / TX) * (((rows > 0 ? rows : H - row0) + TY - 1) / TY);
+    want_carry = tiles >= kCarryMinTilesPerCta * device_sms();
+  }
   if constexpr (C::TMA_OK) {
-    tma = encode_f_map(&map, in, H, W, pitch, C::TMA_BW, C::HROWS_P);
+    if (!want_carry) tma = encode_f_map(&map, in, H, W, pitch, C::TMA_BW, C::HROWS_P);
     if (tma) {
       static int occ_t[64] = {0};
       static int sms_t[64] = {0};
@@ -278,11 +289,7 @@ int launch_cfg(const DeviceParams& dp, const float* in, float* out, int H, int W
   sc.wtot = w.tiles * w.wtile;
   long long G = (long long)nsm * nocc;
   if (G > sc.wtot) G = sc.wtot;
-  // Carried x-pass rows pay when each CTA's range covers several tiles of a strip (the
-  // first tile of a range convolves all its rows); radii <= 15 gain no whole x-pass round.
-  constexpr int CSLOT = 2 * carry_rows(RAD, 4) * TX;
-  constexpr bool kCarryCfg = RAD > 15;
-  const bool carry = kCarryCfg && !tma && w.tiles >= kCarryMinTilesPerCta * G;
+  const bool carry = want_carry && !tma && w.tiles >= kCarryMinTilesPerCta * G;
   if constexpr (kCarryCfg) {
     if (carry) {
       static int occ_c[64] = {0};
@@ -324,10 +331,12 @@ int launch_cfg(const DeviceParams& dp, const float* in, float* out, int H, int W
 
 }  // namespace
 
-int fp32_tile_rows(int r) {
+int fp32_tile_rows(int r, int W, int rows) {
+  const long long strips = (W + TX - 1) / TX, many = kCarryMinTilesPerCta * device_sms();
   if (r <= 6) return 112;
+  if (r <= 9) return 96;
   if (r <= 15) return 96;
-  if (r <= 30) return 128;
+  if (r <= 30) return strips * ((rows + 95) / 96) >= many ? 96 : 128;
   return 64;
 }
 
@@ -340,6 +349,9 @@ int launch_fp32(const DeviceParams& dp, const float* in, float* out, int H, int 
   if (r <= 3) return launch_cfg<3, 112, 512, 7>(dp, in, out, H, W, pitch, st, row0, rows);
   if (r <= 6) return launch_cfg<6, 112, 512, 7>(dp, in, out, H, W, pitch, st, row0, rows);
   if (r <= 9) return launch_cfg<9, 96, 512, 6>(dp, in, out, H, W, pitch, st, row0, rows);
+  // (a 112-row configuration carrying rows at r <= 15, 2 instead of 3 x-pass rounds per
+  // tile, measured slower than these 96-row tiles with TMA staging: 2.59-2.62 against
+  // 2.54 ms at 4096^2, theta 5, K 12)
   if (r <= 15) return launch_cfg<15, 96, 512, 6>(dp, in, out, H, W, pitch, st, row0, rows);
   // 15 < r <= 30: images with at least three 96-row tiles per SM carry their x-pass rows
   // down the strips in a 96-row, 12-warp configuration; others take 128-row tiles, 8 warps

@@ -174,6 +174,8 @@ struct Work {
   int counter_base;                   // index of the image's first tile counter
   int param_idx;                      // index of the image's DeviceParams (work-lists)
   int row0;                           // image row of the first tile row (a band of rows)
+  int row1;                           // image row past the last output row (<= H): a band's
+                                      // last tile row may reach beyond it, writing nothing there
 };
 
 struct Scratch {
@@ -243,6 +245,13 @@ struct SingleSrcCarry {
 // rows of the x-pass buffer a tile can take over from the tile above: the largest multiple
 // of the row-group height (4 rows for k >= 1, 8 for k = 0) not above 2r
 __host__ __device__ constexpr int carry_rows(int rad, int group) { return (2 * rad) / group * group; }
+
+// whether carrying rows saves a whole x-pass round of a tile (4 rows per warp and round for
+// k >= 1): the configurations for which the carried-row kernels are instantiated
+__host__ __device__ constexpr bool carry_saves_round(int rad, int ty, int nt) {
+  return ((ty + 2 * rad + 3) / 4 * 4 - carry_rows(rad, 4) + 4 * (nt / 32) - 1) / (4 * (nt / 32)) <
+         ((ty + 2 * rad + 3) / 4 * 4 + 4 * (nt / 32) - 1) / (4 * (nt / 32));
+}
 
 // A device work-list of images (batched launch); with CARRY, each image's tiles are numbered
 // down its strips and x-pass rows are carried as for SingleSrcCarry, within one image.
@@ -771,7 +780,7 @@ __device__ __forceinline__ void fbf_body(const Src& src, const Scratch& sc) {
 #pragma unroll
       for (int a = 0; a < NY; ++a) {
         const int gy = ty0 + oy + a, gx = tx0 + ox;
-        if (gy < H && gx < W) {
+        if (gy < wk.row1 && gx < W) {
           const float d = den[a];
           const float f = fh[(oy + a + RAD) * FS + ox + RAD];
           __stcs(out + (long)gy * pitch + gx, (d > 0.f) ? m + num[a] / d : f);   // streamed

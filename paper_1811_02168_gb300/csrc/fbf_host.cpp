@@ -125,7 +125,7 @@ extern "C" int fbf_filter_host(fbf_plan_t plan, const float* host_in, float* hos
   // bands of whole tile rows (so each at least r rows), at most kMaxBands, and each with at
   // least two tiles per SM: a band launch with fewer tiles per CTA splits more of them and
   // stages f more often, which costs more than the copies its band hides
-  const int ty = (prec == FBF_FP32) ? fbf::fp32_tile_rows(r)
+  const int ty = (prec == FBF_FP32) ? fbf::fp32_tile_rows(r, W, H / kMaxBands)
                                     : fbf::tc_tile_rows(r <= 6 ? 6 : r <= 15 ? 15 : 30, prec);
   const int tx = (prec == FBF_FP32) ? 32 : 128;
   int sms = 0;

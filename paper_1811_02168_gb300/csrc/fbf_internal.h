@@ -105,7 +105,8 @@ void clear_error();
 // from the whole image.
 int launch_fp32(const DeviceParams& dp, const float* in, float* out, int H, int W,
                 size_t pitch, void* stream, int row0 = 0, int rows = 0);
-int fp32_tile_rows(int r);                  // tile height of the FP32 configuration serving r
+// tile height of the FP32 configuration serving radius r on a launch of `rows` rows of width W
+int fp32_tile_rows(int r, int W, int rows);
 // Per-(device, stream) scratch: `counters` zeroed ints (left at zero by every launch) and
 // `partial_bytes` of partial sums; grown with cudaMalloc when too small.
 int get_workspace(int dev, cudaStream_t_ st, size_t partial_bytes, size_t counters,

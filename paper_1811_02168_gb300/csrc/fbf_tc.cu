@@ -959,7 +959,7 @@ __device__ __forceinline__ void tc_body(const Src& src, const Scratch& sc) {
 #pragma unroll
           for (int a = 0; a < PX; ++a) {
             const int gy = ty0 + oy0 + a;
-            if (gy < H) {
+            if (gy < cw.row1) {
               const float d = dn[a];
               const float f = __ldg(cw.in + (long long)gy * pitch + gx);
               cw.out[(long long)gy * pitch + gx] = (d > 0.f) ? m + nm[a] / d : f;
@@ -1037,6 +1037,7 @@ int launch_rad(const DeviceParams& dp, const float* in, float* out, int H, int W
   w.tiles_x = (W + TILE_X - 1) / TILE_X;
   w.tiles_y = (rows + C::TY - 1) / C::TY;
   w.row0 = row0;
+  w.row1 = row0 + rows;
   w.K = dp.K;
   w.wtile = 2 * dp.K - 1;
   w.tiles = (long long)w.tiles_x * w.tiles_y;

@@ -54,7 +54,10 @@ def test_fp32_instantiation_name():
     assert bench._fp32_kernel_name([plan15], [job]) == "fbf_fp32_tma_kernel"
     assert bench._fp32_kernel_name([plan30], [job]) == "fbf_fp32_kernel"
     assert bench._fp32_kernel_name([plan15], [odd]) == "fbf_fp32_kernel"
-    # r > 15 with at least three 32 x 128 tiles per SM: rows carried down the strips
+    # r > 15 with at least three 32 x 96 tiles per SM: rows carried down the strips; r <= 15
+    # never carries
     big = SimpleNamespace(W=4096, H=4096)
     assert bench._fp32_kernel_name([plan30], [big]) == "fbf_fp32_carry_kernel"
     assert bench._fp32_kernel_name([plan30], [big], sm_count=2000) == "fbf_fp32_kernel"
+    assert bench._fp32_kernel_name([plan15], [big]) == "fbf_fp32_tma_kernel"
+    assert bench._fp32_kernel_name([SimpleNamespace(radius=9)], [big]) == "fbf_fp32_tma_kernel"

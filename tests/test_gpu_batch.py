@@ -406,3 +406,72 @@ def test_batch_mixes_spatial_kernels_within_a_radius_class(B):
         ref = ofl.fourier_bf(img.astype(np.float64), theta, op.c, op.T)
         assert np.abs(y.cpu().numpy() - ref).max() <= TOL, (theta, sigma, K)
     batch.close()
+
+
+_CAND_CHILD = r"""
+import json, sys
+import numpy as np
+import torch
+sys.path.insert(0, sys.argv[1])
+from paper_1811_02168_gb300 import binding as B
+from paper_1811_02168_gb300.synth import voronoi_image
+from oracle import fit as ofit, filters as ofl
+B.lib()
+theta = float(sys.argv[2])
+specs = [(700, 300, 30.0, 6), (450, 520, 10.0, 12), (300, 700, 80.0, 4)]   # K fitted at eps 0.01
+batch = B.Batch(8, autotune=True)
+items = []
+for i, (H, W, sigma, K) in enumerate(specs):
+    img = voronoi_image(H, W, 12, 30.0, 10.0, seed=5100 + i)
+    plan = B.Plan(sigma, 255, theta, K=K)
+    x = torch.from_numpy(img).cuda()
+    y = torch.full_like(x, -5.0)
+    batch.submit(plan, x, y)
+    items.append((img, sigma, K, x, y))   # the device images stay alive until the launch ran
+batch.launch()
+torch.cuda.synchronize()
+err = 0.0
+for img, sigma, K, x, y in items:
+    op = ofit.make_plan(sigma, 255, K=K)
+    ref = ofl.fourier_bf(img.astype(np.float64), theta, op.c, op.T)
+    err = max(err, float(np.abs(y.cpu().numpy() - ref).max()))
+print(json.dumps({"err": err, "device_errors": B.fbf_device_errors(True)}))
+batch.close()
+"""
+
+_CANDIDATES = [(6, 2.0, "r6_ty112_nt512"), (6, 2.0, "r6_ty128_nt256"),
+               (15, 5.0, "r15_ty96_nt512"), (15, 5.0, "r15_ty128_nt256"),
+               (24, 8.0, "r24_ty96_nt384_carry"), (24, 8.0, "r24_ty128_nt256_carry"), (24, 8.0, "r24_ty128_nt256"),
+               (30, 10.0, "r30_ty96_nt384_carry"), (30, 10.0, "r30_ty128_nt256_carry"), (30, 10.0, "r30_ty128_nt256"),
+               (30, 10.0, "r30_ty96_nt256"), (48, 16.0, "r48_ty64_nt128_carry"), (48, 16.0, "r48_ty64_nt128")]
+
+
+@pytest.mark.parametrize("rad,theta,cand", _CANDIDATES)
+def test_every_batch_candidate_matches_the_oracle(B, tmp_path, rad, theta, cand):
+    """Each tile configuration of each FP32 work-list class, forced through the tune cache
+    (a "key name" line for the launch's key, so the autotuner takes it without timing the
+    others: no line is appended), filters three images of the class's theta, of different K
+    and shape, within the FP32 tolerance of the oracle (the autotuner's trials of the other
+    candidates are never compared: their outputs are rewritten).  The plans use the K that
+    Algorithm 1 gives at eps = 0.01: a smaller K at sigma = 10 leaves denominators near zero,
+    where errors grow with the output's size."""
+    import json
+    import math
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    child = tmp_path / "child.py"
+    child.write_text(_CAND_CHILD)
+    px = 700 * 300 + 450 * 520 + 300 * 700
+    key = f"{torch.cuda.get_device_name(0).replace(' ', '_')}/r{rad}/px2^{int(math.floor(math.log2(px)))}/K12"
+    cache = tmp_path / "tune.txt"
+    cache.write_text(f"{key} {cand}\n")
+    env = dict(os.environ, FBF_TUNE_CACHE=str(cache))
+    out = subprocess.run([sys.executable, str(child), root, str(theta)], env=env, capture_output=True, text=True,
+                         timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    res = json.loads(out.stdout.strip().splitlines()[-1])
+    assert res["device_errors"] == 0
+    assert res["err"] <= TOL, res
+    assert cache.read_text().strip().split("\n") == [f"{key} {cand}"]   # taken from the cache
