@@ -66,6 +66,8 @@ def _host(B, plan, img, pitch=None, inplace=False, pinned=True):
     (2.0, 30.0, 4, 200, 131),       # one band (r = 6)
     (5.0, 10.0, 12, 2300, 2050),    # r = 15: FP32 4 bands, tensor-core forms 2; width not a multiple of 4
     (10.0, 10.0, 16, 2085, 4099),   # r = 30: FP32 4 bands, tensor-core forms 3; ragged last band
+    (10.0, 30.0, 8, 4096, 1024),    # r = 30, FP32: bands of 1408 rows (11 x 128) whose launches
+                                    # carry rows in 96-row tiles, the last tile row past the band
 ])
 def test_host_call_equals_device_call(B, prec, theta, sigma, K, H, W):
     form = {"fp32": B.FBF_FP32, "bf16_tc": B.FBF_BF16_TC, "fp16_tc": B.FBF_FP16_TC}[prec]
