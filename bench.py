@@ -922,10 +922,14 @@ def _gen_class_image(args):
     return synth.voronoi_image(H, W, synth.scaled_cells(H, W), 40.0, 10.0, seed=seed)
 
 
+def _size_classes(lo, hi, n):
+    """n log-spaced values in [lo, hi] (the request size classes)."""
+    return [int(round(math.exp(math.log(lo) + (math.log(hi) - math.log(lo)) * i / (n - 1)))) for i in range(n)]
+
+
 def _snap_log(v, lo, hi, n):
     """Nearest of n log-spaced values in [lo, hi] (the request size classes)."""
-    grid = [int(round(math.exp(math.log(lo) + (math.log(hi) - math.log(lo)) * i / (n - 1)))) for i in range(n)]
-    return min(grid, key=lambda g: abs(math.log(g) - math.log(v)))
+    return min(_size_classes(lo, hi, n), key=lambda g: abs(math.log(g) - math.log(v)))
 
 
 def run_serve(a):
@@ -962,7 +966,10 @@ def run_serve(a):
     stream_jobs = synth.workload_stream(rate=a.serve_rate, duration=a.serve_seconds)
     backlog_jobs = synth.workload_stream(rate=1e4, duration=a.serve_backlog / 1e4, seed=4500)
     snapped = lambda j: (_snap_log(j.H, 512, 4096, n_cls), _snap_log(j.W, 512, 4096, n_cls))  # noqa: E731
-    classes = sorted({snapped(j) for _, j in stream_jobs} | {snapped(j) for _, j in backlog_jobs})
+    # every size class pair (the rate sweep draws its own requests, whose classes need not
+    # appear in the stream or the backlog)
+    grid = _size_classes(512, 4096, n_cls)
+    classes = [(h, w) for h in grid for w in grid]
     import multiprocessing as mp
     t_gen = time.perf_counter()
     with mp.get_context("spawn").Pool(_host_cores()) as pool:
