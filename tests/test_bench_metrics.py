@@ -61,3 +61,16 @@ def test_fp32_instantiation_name():
     assert bench._fp32_kernel_name([plan30], [big], sm_count=2000) == "fbf_fp32_kernel"
     assert bench._fp32_kernel_name([plan15], [big]) == "fbf_fp32_tma_kernel"
     assert bench._fp32_kernel_name([SimpleNamespace(radius=9)], [big]) == "fbf_fp32_tma_kernel"
+
+
+def test_serve_size_classes_cover_every_request():
+    """The serving workload generates one image per size-class pair for the whole grid, so any
+    request side the Poisson stream, the backlog or a rate sweep draws snaps to a generated
+    class (a short run once drew a class the stream and backlog had not)."""
+    import numpy as np
+    grid = bench._size_classes(512, 4096, 12)
+    assert grid[0] == 512 and grid[-1] == 4096 and len(set(grid)) == 12
+    assert all(a < b for a, b in zip(grid, grid[1:]))
+    rng = np.random.default_rng(0)
+    for v in np.exp(rng.uniform(np.log(512), np.log(4096), 2000)):
+        assert bench._snap_log(float(v), 512, 4096, 12) in grid
