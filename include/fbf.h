@@ -71,6 +71,16 @@ extern "C" {
 #define FBF_BF16       FBF_BF16_TC
 #define FBF_TF32_TC    FBF_BF16_TC
 
+/* FBF_FAST: whichever of FBF_FP32 and FBF_BF16_TC filters faster at the plan's radius
+   r = ceil(3 theta), chosen when the plan is made: FBF_FP32 for r <= FBF_FAST_FP32_MAX_RADIUS
+   (there the short FIR costs less than the tensor-core form's operand generation: on a
+   GB300, work-lists of 256^2-2048^2 images at r = 6 took 0.87 ms in FP32 against 1.30 ms in
+   FBF_BF16_TC, at r = 15 1.13 against 0.88 ms), FBF_BF16_TC for larger r up to
+   FBF_MAX_RADIUS_TC, FBF_FP32 above it.  Its error is that of the chosen form, so within
+   FBF_BF16_TC's bound (0.5 gray levels).  Not in the paper (a scheduling choice).       */
+#define FBF_FAST       3
+#define FBF_FAST_FP32_MAX_RADIUS 6
+
 /* ---- flags (fbf_plan's `flags`) ----------------------------------------------- */
 #define FBF_FLAG_FIXED_PERIOD 1  /* T = R (fixed period, the FBF model the paper
                                     compares against, Section III); least squares only */
@@ -96,7 +106,8 @@ typedef struct fbf_plan_s* fbf_plan_t;
  * {-R..R} is the same for every least-squares solution.
  *
  * sigma > 0, R >= 1, theta > 0 (spatial std; window radius r = ceil(3 theta), the
- * (6 theta + 1)^2 window of Section I), precision one of FBF_FP32..., flags a bitwise OR
+ * (6 theta + 1)^2 window of Section I), precision one of FBF_FP32, FBF_FP16_TC,
+ * FBF_BF16_TC or FBF_FAST (resolved here to FBF_FP32 or FBF_BF16_TC), flags a bitwise OR
  * of FBF_FLAG_*.  Runs on the host only; needs no GPU.  *out receives a handle owned by
  * the caller and released with fbf_plan_destroy.
  * Errors: FBF_EINVAL for bad arguments or a NULL out; FBF_EUNSUPPORTED when the fitted
@@ -316,7 +327,8 @@ typedef struct {
 } fbf_server_stats_t;
 
 /* fbf_server_create -- a server on CUDA device `device` filtering in precision form
- * `precision` (FBF_FP32, FBF_FP16_TC, FBF_BF16_TC).  hbm_budget_bytes >= 1, max_batch >= 1
+ * `precision` (FBF_FP32, FBF_FP16_TC, FBF_BF16_TC, FBF_FAST: each request's plan takes
+ * the faster form for its radius).  hbm_budget_bytes >= 1, max_batch >= 1
  * (requests per launch; 1 = one request per launch), max_inflight >= 1.  The caller's
  * current device is left unchanged.  Errors: FBF_EINVAL, FBF_ENOMEM, FBF_ECUDA. */
 int fbf_server_create(fbf_server_t* out, int device, int precision, uint64_t hbm_budget_bytes,

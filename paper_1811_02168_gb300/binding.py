@@ -21,6 +21,8 @@ FBF_FP32 = 0
 FBF_FP16_TC = 1
 FBF_BF16_TC = 2
 FBF_BF16 = FBF_TF32_TC = FBF_BF16_TC   # the problem statement's names for the compensated form
+FBF_FAST = 3                          # FBF_FP32 or FBF_BF16_TC, whichever is faster at the radius
+FBF_FAST_FP32_MAX_RADIUS = 6
 FBF_FLAG_FIXED_PERIOD = 1
 FBF_MAX_K = 64
 FBF_MAX_RADIUS = 48

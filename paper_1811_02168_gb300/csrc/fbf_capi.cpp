@@ -35,7 +35,7 @@ namespace {
 int radius_of(double theta) { return (int)std::ceil(3.0 * theta - 1e-12); }
 
 bool precision_known(int precision) {
-  return precision == FBF_FP32 || precision == FBF_FP16_TC || precision == FBF_BF16_TC;
+  return precision == FBF_FP32 || precision == FBF_FP16_TC || precision == FBF_BF16_TC || precision == FBF_FAST;
 }
 
 }  // namespace
@@ -59,6 +59,10 @@ int build_plan(fbf_plan_t* out, const double* b, int R, double theta, int K, dou
   const int r = radius_of(theta);
   if (r > FBF_MAX_RADIUS)
     return fbf::set_error(FBF_EUNSUPPORTED, "fbf_plan: radius ceil(3 theta) exceeds FBF_MAX_RADIUS");
+  // FBF_FAST: the faster form at this radius (FP32 for short windows and beyond the
+  // tensor-core limit, the compensated BF16 tensor-core form between)
+  if (precision == FBF_FAST)
+    precision = (r <= FBF_FAST_FP32_MAX_RADIUS || r > FBF_MAX_RADIUS_TC) ? FBF_FP32 : FBF_BF16_TC;
   if (precision != FBF_FP32 && r > FBF_MAX_RADIUS_TC)
     return fbf::set_error(FBF_EUNSUPPORTED, "fbf_plan: the tensor-core forms support r <= FBF_MAX_RADIUS_TC");
   if (K > FBF_MAX_K) return fbf::set_error(FBF_EUNSUPPORTED, "fbf_plan: K exceeds FBF_MAX_K");

@@ -312,7 +312,7 @@ int get_plan(fbf_server_s* s, double sigma, int R, double theta, int K, double e
   if (rc != FBF_OK) return rc;
   int r = 0;
   fbf_plan_radius(p, &r);
-  const int rmax = (s->precision == FBF_FP32) ? FBF_MAX_RADIUS : FBF_MAX_RADIUS_TC;
+  const int rmax = (s->precision == FBF_FP32 || s->precision == FBF_FAST) ? FBF_MAX_RADIUS : FBF_MAX_RADIUS_TC;
   if (r > rmax) {
     fbf_plan_destroy(p);
     return fbf::set_error(FBF_EUNSUPPORTED, "fbf_server_submit: radius beyond the form's limit");
@@ -344,7 +344,7 @@ int fbf_server_create(fbf_server_t* out, int device, int precision, uint64_t hbm
                       int max_batch, int max_inflight) try {
   if (!out) return fbf::set_error(FBF_EINVAL, "fbf_server_create: out is NULL");
   *out = nullptr;
-  if (precision != FBF_FP32 && precision != FBF_FP16_TC && precision != FBF_BF16_TC)
+  if (precision != FBF_FP32 && precision != FBF_FP16_TC && precision != FBF_BF16_TC && precision != FBF_FAST)
     return fbf::set_error(FBF_EINVAL, "fbf_server_create: unknown precision form");
   if (max_batch < 1 || max_inflight < 1 || hbm_budget_bytes == 0)
     return fbf::set_error(FBF_EINVAL, "fbf_server_create: max_batch, max_inflight and the budget must be >= 1");

@@ -243,6 +243,19 @@ def test_precision_names_of_the_problem_statement():
     assert p.K == 4
 
 
+def test_fast_form_takes_fp32_where_tensor_cores_cannot():
+    """FBF_FAST is resolved when the plan is made: beyond the tensor-core radius limit it is
+    the FP32 form (a plan FBF_BF16_TC refuses), and any other precision value is refused."""
+    with pytest.raises(B.FbfError) as ei:
+        B.Plan(30.0, 255, 16.0, K=4, precision=B.FBF_BF16_TC)      # r = 48 > FBF_MAX_RADIUS_TC
+    assert ei.value.code == B.FBF_EUNSUPPORTED
+    for theta in (2.0, 5.0, 10.0, 16.0):                          # r = 6, 15, 30, 48
+        assert B.Plan(30.0, 255, theta, K=4, precision=B.FBF_FAST).K == 4
+    with pytest.raises(B.FbfError) as ei:
+        B.Plan(30.0, 255, 2.0, K=4, precision=7)
+    assert ei.value.code == B.FBF_EINVAL
+
+
 def test_failed_launch_empties_the_queue():
     """A launch or capture that fails (here: no CUDA device) still empties the queue, so
     images whose buffers the caller frees after the error are never launched later.  The

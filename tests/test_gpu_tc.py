@@ -137,3 +137,19 @@ def test_bf16_wide_radius_half_row_items(B, noninteger):
     ref = ofl.fourier_bf(img.astype(np.float64), 10.0, op.c, op.T)
     assert float(np.abs(_run(B, plan, img) - ref).max()) <= TOL["bf16"]
     assert B.fbf_device_errors() == 0
+
+
+@pytest.mark.parametrize("theta,form", [(2.0, "fp32"), (3.0, "bf16_tc"), (5.0, "bf16_tc"), (10.0, "bf16_tc"),
+                                        (16.0, "fp32")])
+def test_fast_form_runs_the_faster_kernel_of_its_radius(B, theta, form):
+    """FBF_FAST plans run the FP32 kernel at r <= 6 and beyond the tensor-core limit (r = 48)
+    and the compensated BF16 tensor-core kernel between (r = 9, 15, 30): bit for bit the
+    result of a plan made with that form, and within the 0.5 bound of the oracle."""
+    img = voronoi_image(200, 230, 14, 40.0, 10.0, seed=int(theta * 10))
+    prec = {"fp32": B.FBF_FP32, "bf16_tc": B.FBF_BF16_TC}[form]
+    fast = _run(B, B.Plan(30.0, 255, theta, K=6, precision=B.FBF_FAST), img)
+    same = _run(B, B.Plan(30.0, 255, theta, K=6, precision=prec), img)
+    assert np.array_equal(fast, same)
+    op = ofit.make_plan(30.0, 255, K=6)
+    ref = ofl.fourier_bf(img.astype(np.float64), theta, op.c, op.T)
+    assert np.abs(fast - ref).max() <= (5e-3 if form == "fp32" else 0.5)
