@@ -61,6 +61,9 @@ def _args():
                     help="length of each open-loop run of the serving rate sweep")
     ap.add_argument("--serve-idle-sleep", type=float, default=5e-5,
                     help="python loop: seconds it sleeps when it has nothing to do (0: poll)")
+    ap.add_argument("--serve-mode", default=None,
+                    help="serve workload: run this one mode and print its results (the parent runs every "
+                         "mode in a fresh process of its own)")
     ap.add_argument("--serve-loop", choices=["native", "python"], default="native",
                     help="serving loop: the library's (fbf_server_*) or serve.py's")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -988,6 +991,8 @@ def run_serve(a):
     class pair drawn is generated with the small workload's recipe (spawned processes),
     so every request filters a full Voronoi mosaic of its own size.  Results of unchecked
     requests go to a pinned ring.  Single GPU."""
+    if a.serve_mode is None:
+        return _serve_parent(a)
     import numpy as np
     import torch
 
@@ -1088,9 +1093,10 @@ def run_serve(a):
                 "sample": f"{len(errs)} served requests x 300 sampled pixels against the FP64 oracle"}
 
     results = {}
-    clocks = ClockSampler(0)
-    clocks.start()
+    assert [m[0] for m in modes] == list(SERVE_MODES)
     for mode, prec, batching in modes:
+        if mode != a.serve_mode:
+            continue
         res = {}
         reqs = make_requests(stream_jobs)
         check = sorted(range(len(reqs)), key=lambda i: reqs[i].H * reqs[i].W)[:3]
@@ -1109,6 +1115,8 @@ def run_serve(a):
     # rate sweep around each main mode's capacity
     mean_px = statistics.mean(r.H * r.W for r in make_requests(backlog_jobs))
     for mode, prec, batching in modes[:2]:
+        if mode != a.serve_mode:
+            continue
         cap_rps = results[mode]["capacity"]["mpix_per_s"] * 1e6 / mean_px
         sweep = []
         for frac in (0.25, 0.5, 0.75, 0.9, 1.1):
@@ -1129,24 +1137,56 @@ def run_serve(a):
                 knee = s
         results[mode]["rate_sweep"] = sweep
         results[mode]["knee"] = knee
+    print(json.dumps({"serve_mode": a.serve_mode, "result": results[a.serve_mode], "image_generation_s": t_gen,
+                      "backlog_requests": len(backlog_jobs), "warm_params": len(warm_params)}), flush=True)
+    return 0
+
+
+# serving modes, in their order in the line: the chosen form, the plain form, then the others
+SERVE_MODES = ("continuous_batching_fast", "one_at_a_time_fp32", "continuous_batching", "continuous_batching_fp32")
+
+
+def _serve_parent(a):
+    """Runs every serving mode in a fresh process of its own (python bench.py --workload serve
+    --serve-mode M), one after another, and prints the line.  Within one process, modes run
+    after the first one were measured slower in every respect (the first mode's numbers were
+    the best whichever mode it was), which would favour the mode run first."""
+    import subprocess
+    results, child = {}, {}
+    clocks = ClockSampler(0)
+    clocks.start()
+    for mode in SERVE_MODES:
+        cmd = [sys.executable, os.path.abspath(__file__), "--workload", "serve", "--serve-mode", mode,
+               "--serve-seconds", str(a.serve_seconds), "--serve-rate", str(a.serve_rate),
+               "--serve-backlog", str(a.serve_backlog), "--serve-sweep-seconds", str(a.serve_sweep_seconds),
+               "--serve-idle-sleep", str(a.serve_idle_sleep), "--serve-loop", a.serve_loop]
+        out = subprocess.run(cmd, capture_output=True, text=True)
+        if out.returncode != 0:
+            sys.stderr.write(out.stderr[-4000:])
+            return out.returncode
+        child = json.loads(out.stdout.strip().splitlines()[-1])
+        results[mode] = child["result"]
     clk = clocks.stop()
     cb = results["continuous_batching_fast"]
     one = results["one_at_a_time_fp32"]
+    n_cls = 12
+    t_gen = child["image_generation_s"]
     line = {
         "metric": METRIC, "value": cb["capacity"]["mpix_per_s"], "unit": "Mpix/s", "n_gpus": 1,
-        "steps": cb["capacity"]["requests"], "warmup": len(warm_params),
+        "steps": cb["capacity"]["requests"], "warmup": child["warm_params"],
         "ms_per_step": 1e3 * cb["capacity"]["wall_s"] / max(1, cb["capacity"]["requests"]),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "latency_ms": {"p50": cb["open_loop"]["p50_ms"], "p99": cb["open_loop"]["p99_ms"],
                        "at_offered_req_per_s": a.serve_rate},
         "config": {"workload": "serve_poisson", "rate_per_s": a.serve_rate, "seconds": a.serve_seconds,
                    "sides": [512, 4096], "size_classes_per_side": n_cls, "hbm_budget_gb": 40,
-                   "backlog_requests": len(backlog_jobs), "form": "fast (per request the faster of FP32 and the "
-                   "compensated BF16 stack on the tensor cores at its radius: FP32 at r <= 6, BF16_TC above)",
+                   "backlog_requests": child["backlog_requests"], "form": "fast (per request the faster of FP32 "
+                   "and the compensated BF16 stack on the tensor cores at its radius: FP32 at r <= 6, BF16_TC above)",
                    "baseline_form": "fp32, one request per launch",
                    "loop": ("the library's serving loop (fbf_server_*, native worker thread; requests replayed "
                             "at their arrival times by fbf_server_replay)" if a.serve_loop == "native"
                             else "serve.py's Python loop over the batch API"),
+                   "processes": "one fresh process per mode, modes in the order of `served`",
                    "image_generation_s": t_gen, "served": results,
                    "note": "value = sustained Mpix/s of FBF_FAST continuous batching on a backlog (capacity); "
                            "latency at the open-loop rate"},
