@@ -61,7 +61,7 @@ def _args():
                     help="length of each open-loop run of the serving rate sweep")
     ap.add_argument("--serve-idle-sleep", type=float, default=5e-5,
                     help="python loop: seconds it sleeps when it has nothing to do (0: poll)")
-    ap.add_argument("--serve-mode", default=None,
+    ap.add_argument("--serve-mode", default=None, choices=list(SERVE_MODES),
                     help="serve workload: run this one mode and print its results (the parent runs every "
                          "mode in a fresh process of its own)")
     ap.add_argument("--serve-loop", choices=["native", "python"], default="native",
