@@ -1142,6 +1142,51 @@ def run_serve(a):
     return 0
 
 
+class HostSampler:
+    """Samples the host once a second while serving modes run: the 1-minute load average and,
+    where the kernel exposes them, the CPUs' current clocks (cpufreq, else /proc/cpuinfo).
+    Read-only; records nothing when neither is available."""
+
+    def __init__(self):
+        import threading
+        self.rows, self._stop = [], threading.Event()
+        self._t = threading.Thread(target=self._run, daemon=True)
+
+    @staticmethod
+    def _mhz():
+        vals = []
+        for i in range(os.cpu_count() or 1):
+            try:
+                with open(f"/sys/devices/system/cpu/cpu{i}/cpufreq/scaling_cur_freq") as fh:
+                    vals.append(int(fh.read()) / 1000.0)
+            except OSError:
+                break
+        if not vals:
+            try:
+                with open("/proc/cpuinfo") as fh:
+                    vals = [float(ln.split(":")[1]) for ln in fh if ln.lower().startswith("cpu mhz")]
+            except (OSError, ValueError, IndexError):
+                vals = []
+        return statistics.mean(vals) if vals else None
+
+    def _run(self):
+        t0 = time.time()
+        while not self._stop.wait(1.0):
+            self.rows.append((time.time() - t0, os.getloadavg()[0], self._mhz()))
+
+    def start(self):
+        self._t.start()
+
+    def stop(self):
+        self._stop.set()
+        self._t.join(timeout=5)
+        mhz = [r[2] for r in self.rows if r[2] is not None]
+        return {"samples": len(self.rows), "load1_max": max((r[1] for r in self.rows), default=None),
+                "cpu_mhz_median": statistics.median(mhz) if mhz else None,
+                "cpu_mhz_min": min(mhz) if mhz else None,
+                "cpu_mhz_source": "cpufreq scaling_cur_freq, else /proc/cpuinfo (mean over CPUs, 1 s samples)"}
+
+
 # serving modes, in their order in the line: the chosen form, the plain form, then the others
 SERVE_MODES = ("continuous_batching_fast", "one_at_a_time_fp32", "continuous_batching", "continuous_batching_fp32")
 
@@ -1160,12 +1205,16 @@ def _serve_parent(a):
                "--serve-seconds", str(a.serve_seconds), "--serve-rate", str(a.serve_rate),
                "--serve-backlog", str(a.serve_backlog), "--serve-sweep-seconds", str(a.serve_sweep_seconds),
                "--serve-idle-sleep", str(a.serve_idle_sleep), "--serve-loop", a.serve_loop]
+        host = HostSampler()
+        host.start()
         out = subprocess.run(cmd, capture_output=True, text=True)
+        host_rec = host.stop()
         if out.returncode != 0:
             sys.stderr.write(out.stderr[-4000:])
             return out.returncode
         child = json.loads(out.stdout.strip().splitlines()[-1])
         results[mode] = child["result"]
+        results[mode]["host"] = host_rec
     clk = clocks.stop()
     cb = results["continuous_batching_fast"]
     one = results["one_at_a_time_fp32"]
