@@ -74,3 +74,15 @@ def test_serve_size_classes_cover_every_request():
     rng = np.random.default_rng(0)
     for v in np.exp(rng.uniform(np.log(512), np.log(4096), 2000)):
         assert bench._snap_log(float(v), 512, 4096, 12) in grid
+
+
+def test_host_sampler_records_load_and_stops():
+    """The serving bench's host sampler (load average, CPU clocks where exposed) samples once
+    a second on its own thread and stops on request."""
+    import time
+    h = bench.HostSampler()
+    h.start()
+    time.sleep(1.3)
+    rec = h.stop()
+    assert rec["samples"] >= 1 and rec["load1_max"] >= 0.0
+    assert rec["cpu_mhz_median"] is None or rec["cpu_mhz_median"] > 0
