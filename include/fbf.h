@@ -165,8 +165,8 @@ int fbf_filter(fbf_plan_t plan, const float* d_in, float* d_out, int H, int W,
  * compiled into the library, which every GPU that loads the library holds until exit.
  * It calls no cudaMalloc, cudaFree or allocating library routine.
  *
- * Arguments, layout and results are those of fbf_filter (FBF_FP32 plans only, else
- * FBF_EUNSUPPORTED).  The first call on a device looks up the array's device address
+ * Arguments, layout and results are those of fbf_filter (FBF_FP32 plans only, among them
+ * FBF_FAST plans that took the FP32 form; else FBF_EUNSUPPORTED).  The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call before any
  * stream capture.  The address is kept for the life of the process: after a
  * cudaDeviceReset no entry point may be called again in that process (this address and the
